@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark: accepted system-steps per second of the per-thread ODE
+integrators on synthetic sweeps shaped like the paper's test cases.
+
+Default workload: Duffing oscillator x'' + k x' + x + x^3 = B cos t on a
+512 x 256 grid (k in [0.2, 0.3], B in [0.3, 0.5]), 2^17 systems, binary64
+RKCK45 rtol = atol = 1e-10, h0 = 1e-2, local-maximum event y2 = 0 located to
+1e-12, 1024 transient + 64 recorded periods of 2 pi.  One benchmark step is
+one whole pass: reset the initial conditions from HBM, integrate every system
+over all 1088 periods in one persistent launch, write the 64 records.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--workload duffing_rkck|duffing_rk4|valve|keller_miksis]
+Under torchrun each rank integrates its own sweep (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+# Algorithmic binary64 flops per accepted step, counted from the kernel's
+# formulas (add, mul = 1; fma = 2; the transcendental calls are listed
+# separately and not counted).  Duffing RKCK45: 6 right-hand sides x 10
+# (= 60), stage times 10, stage states 70, update 18, error estimate 20,
+# error norm 10, step-size controller 20, time update 1  -> 209 (+ 6 cos).
+# Duffing RK4: 4 x 10 + stage times 4 + stage states 14 + update 18 + 1 = 77
+# (+ 4 cos).  Valve RKCK45: 6 x 11 + 10 + 105 + 27 + 30 + 15 + 20 + 1 = 274
+# (+ 6 sqrt).  Keller-Miksis RKCK45: 6 x 36 + 10 + 70 + 18 + 20 + 10 + 20 + 1
+# = 365 (+ 6 pow, 6 sincospi, 12 div).
+FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365}
+METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
+UNIT = "system-steps/s"
+
+
+def workload(name, rank=0):
+    if name == "duffing_rkck":
+        w = W.duffing_rkck()
+        # weak scaling: rank r sweeps its own band of B above the base grid
+        w["p"] = w["p"].copy()
+        w["p"][1] += 0.2 * rank
+        return w
+    if name == "duffing_rk4":
+        return W.duffing_rk4()
+    if name == "valve":
+        return W.valve()
+    if name == "keller_miksis":
+        return W.keller_miksis(n_transient=16, n_record=16)
+    raise SystemExit("unknown workload %s" % name)
+
+
+def describe(w, persistent, l2):
+    d = {"workload": w["name"], "systems": w["N"], "periods": w["n_transient"] + w["n_record"],
+         "recorded_periods": w["n_record"], "scheme": "RKCK45" if w["scheme"] == 1 else "RK4",
+         "rtol": w["rtol"], "launch": "persistent work queue" if persistent else "one thread per system",
+         "l2": l2}
+    if w["events_on"]:
+        d["events"] = "y2=0 dir -1 located to %g" % w["evt_tol"][0] if w["model"] == 0 else "2 events"
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_1810_03931_gb300 import build as B
+    from paper_1810_03931_gb300 import odegpu as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    G.load(build_if_missing=False)
+
+    from _runners import DIMS, km_params_gpu
+
+    w = workload(args.workload, rank)
+    n, P, A, E = DIMS[w["model"]]
+    N = w["N"]
+    n_tr, n_rec = w["n_transient"], w["n_record"]
+    R = A + n + 1
+    stream = torch.cuda.current_stream(dev)
+
+    s = G.ode_create(w["model"], w["scheme"], G.ODE_FP64, N, local)
+    G.ode_set_tolerances(s, np.full(n, w["rtol"]), np.full(n, w["atol"]), w["hmax"], w["hmin"], w["grow"],
+                         w["shrink"])
+    G.ode_set_events(s, int(w["events_on"]), np.array(w["evt_dir"][:E], dtype=np.int32),
+                     np.array(w["evt_tol"][:E]), np.array(w["evt_stop"][:E], dtype=np.int32), w["max_eq"])
+    if w["mc"]:
+        G.ode_set_model_constants(s, np.array(w["mc"], dtype=np.float64))
+    G.ode_set_time_domain_mode(s, w["td_mode"])
+    G.ode_set_launch(s, args.block, args.persistent)
+
+    params = km_params_gpu(w) if w["model"] == 1 else w["p"]
+    # resident inputs (HBM) and the records buffer
+    d_td = torch.tensor(w["td"], dtype=torch.float64, device=dev)
+    d_y0 = torch.tensor(w["y0"], dtype=torch.float64, device=dev)
+    d_p = torch.tensor(params, dtype=torch.float64, device=dev)
+    d_acc = torch.zeros((A, N), dtype=torch.float64, device=dev)
+    d_rec = torch.zeros((n_rec, R, N), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    nacc = np.zeros(N, dtype=np.int64)
+
+    def step():
+        G.ode_reset_counters(s, stream)
+        G.ode_linear_set(s, 0, 0, N, N, td=d_td, y=d_y0, p=d_p, acc=d_acc, copy_mode=G.ODE_ALL, stream=stream)
+        G.ode_run_periods(s, w["h0"], n_tr, n_rec, d_rec, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    acc_steps = []
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        G.ode_get_status(s, accepted=nacc, stream=stream)  # host copy: synchronizes
+        acc_steps.append(int(nacc.sum()))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = sum(ms) / len(ms)
+    steps_per_pass = float(np.mean(acc_steps))
+
+    # end to end through the C ABI with host buffers: H2D of the inputs, the
+    # integration, D2H of the records and the per-system step counts
+    h_td = torch.tensor(w["td"], dtype=torch.float64).pin_memory()
+    h_y0 = torch.tensor(w["y0"], dtype=torch.float64).pin_memory()
+    h_p = torch.tensor(params, dtype=torch.float64).pin_memory()
+    h_acc = torch.zeros((A, N), dtype=torch.float64).pin_memory()
+    h_rec = torch.zeros((n_rec, R, N), dtype=torch.float64).pin_memory()
+    h_nacc = torch.zeros(N, dtype=torch.int64).pin_memory()
+    e2e_times, e2e_steps = [], []
+    for k in range(max(1, min(args.steps, 2))):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.ode_reset_counters(s, stream)
+        G.ode_linear_set(s, 0, 0, N, N, td=h_td, y=h_y0, p=h_p, acc=h_acc, copy_mode=G.ODE_ALL, stream=stream)
+        G.ode_run_periods(s, w["h0"], n_tr, n_rec, h_rec, stream=stream)
+        G.ode_get_status(s, accepted=h_nacc, stream=stream)
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_steps.append(int(h_nacc.numpy().sum()))
+    h2d = 8 * (2 + n + P + A) * N
+    d2h = 8 * n_rec * R * N + 8 * N
+
+    # roofline peak: binary64 FMA units per SM (2, measured by the probe
+    # below as FMA per clock per SM) x SMs x maximum SM clock x 2 flops
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    max_mhz = None
+    if os.path.exists(peaks_path):
+        max_mhz = json.load(open(peaks_path)).get("sm_max_mhz")
+    if not max_mhz:
+        max_mhz = clk.get("sm_max_mhz") or 2070.0
+    dfma, ffma = G.ode_probe_fma_peak(local)
+    peak_tflops = 2 * 2 * sms * max_mhz * 1e6 / 1e12
+    flops = FLOPS_PER_STEP.get(args.workload, 0) * steps_per_pass
+    achieved_tflops = flops / (ms_step * 1e-3) / 1e12
+
+    G.ode_destroy(s)
+
+    # aggregate over ranks: total accepted steps / max time
+    tot_steps, max_ms = steps_per_pass, ms_step
+    e2e_rate = float(np.mean(e2e_steps)) / float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([tot_steps, 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        m = torch.tensor([max_ms, float(np.mean(e2e_times))], dtype=torch.float64, device=dev)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        tot_steps, max_ms = float(t[0]), float(m[0])
+        e2e_rate = float(np.mean(e2e_steps)) * world / float(m[1])
+
+    line = None
+    if rank == 0:
+        value = tot_steps / (max_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, args.persistent, "flushed before every timed step (256 MB write)"),
+            "accepted_steps_per_pass": steps_per_pass, "wall_s_timed": wall,
+            "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "s_per_step": float(np.mean(e2e_times))},
+            "gpu_launches": args.steps,  # one integrator launch per step
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "peak_basis": "2 FP64 FMA/clk/SM x %d SMs x %.0f MHz x 2 (derived; live probe %.3f TFLOP/s)"
+                                       % (sms, max_mhz, 2 * dfma / 1e12),
+                         "flops_per_step": FLOPS_PER_STEP.get(args.workload, 0)},
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1 or (world > 1 and not args.no_cpu_baseline):
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: timed on the host cores on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def _oracle_rate(w, n_sys, nthreads):
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _runners import run_oracle
+    idx = W.sample_indices(w["N"], n_sys)
+    ws = W.subset(w, idx)
+    t0 = time.perf_counter()
+    r = run_oracle(ws, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return float(r["nacc"].sum()) / dt, dt, len(idx)
+
+
+def cpu_baseline(w, seconds):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # calibrate on a few systems, then size the sample to ~`seconds` of wall
+    rate1, dt1, n1 = _oracle_rate(w, cores, cores)
+    per_sys = dt1 / max(1, n1) * cores
+    n_sys = int(max(cores, min(w["N"], seconds / max(per_sys, 1e-6) * cores)))
+    rate, dt, n = _oracle_rate(w, n_sys, cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d systems (seeded), all %d periods, %.1f s wall on %d threads"
+                      % (n, w["N"], w["n_transient"] + w["n_record"], dt, cores)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload(args.workload)
+    cores = os.cpu_count() or 1
+    budget = max(10.0, 150.0 / max(1, args.steps + args.warmup))
+    rate1, dt1, n1 = _oracle_rate(w, cores, cores)
+    n_sys = int(max(cores, min(w["N"], budget / max(dt1 / n1 * cores, 1e-6) * cores)))
+    for _ in range(args.warmup):
+        _oracle_rate(w, max(cores, n_sys // 4), cores)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, n = _oracle_rate(w, n_sys, cores)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, 0, "n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d of %d systems (seeded) per step, all periods" % (n_sys, w["N"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="duffing_rkck",
+                    choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis"])
+    ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * odegpu.h -- C ABI of the GB300 (sm_103a) library that integrates very many
+ * independent, identical, low-order ODE systems, one system per GPU thread,
+ * after F. Hegedus, "Modular, general purpose ODE integration package to solve
+ * large number of independent ODE systems on GPUs" (arXiv:1810.03931).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value: int status, ODE_OK (0) on success, a negative ODE_ERR_* code
+ *   otherwise.  The message of the last failure is returned by
+ *   ode_last_error(solver) (or ode_last_error(NULL) for failures that have no
+ *   solver, e.g. ode_create).  A failed call leaves the solver usable unless
+ *   the CUDA context itself was lost (ODE_ERR_CUDA with a sticky CUDA error).
+ * Layout: every per-system array is structure-of-arrays, component-major:
+ *   value[component * stride + system], as the problem pool of Sec. 6.1 of the
+ *   paper prescribes (Fig. "problem pool"; the index idx + i*NoT of Sec. 6.5).
+ *   All floating-point data are IEEE binary64 (double).
+ * Ownership: the solver owns all of its device buffers (allocated by
+ *   ode_create, freed by ode_destroy).  Caller buffers are only read or
+ *   written during the call (or, for calls that take a stream, by work
+ *   enqueued on that stream); no call keeps a caller pointer after it returns.
+ * Pointer kind: calls that take caller arrays have a ptr_kind argument,
+ *   ODE_PTR_HOST (host memory, pageable or pinned) or ODE_PTR_DEVICE (device
+ *   memory of the solver's device, e.g. a torch CUDA tensor's data_ptr()).
+ * Streams: a `void *stream` argument is a cudaStream_t (NULL = the legacy
+ *   default stream).  Calls with ODE_PTR_HOST arrays synchronize that stream
+ *   before returning; calls with device arrays only enqueue work.
+ * Threads: a solver may be used from one host thread at a time.
+ * Nothing on this interface falls back to the CPU: with no usable GPU,
+ *   ode_create fails with ODE_ERR_CUDA.
+ */
+#ifndef ODEGPU_H
+#define ODEGPU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ode_solver ode_solver; /* opaque; the ParametricODESolver object of Sec. 6.2 */
+
+/* Models: the pre-declared device hooks of Sec. 6.5-6.8 are compiled into
+ * the library per model (Sec. 6.9: hooks in the kernels' translation unit).
+ *  ODE_DUFFING        Eqs. (1)-(2): n=2, P=2 (k, B), A=7, E=1 (F0 = y2)
+ *                     solver constants (delta, c3, omega), default (-1, 1, 1)
+ *                     i.e. x'' + k x' + x + x^3 = B cos(omega t);
+ *                     c3 = 0 gives the linear damped forced oscillator.
+ *  ODE_KELLER_MIKSIS  Eqs. (12)-(28): n=2, P=13 (C0..C12), A=4, E=1 (F0 = y2)
+ *  ODE_VALVE          Eqs. (29)-(34): n=3, P=5 (kappa, delta, beta, q, r),
+ *                     A=5, E=2 (F0 = y2, F1 = y1 with impact y2 <- -r y2)
+ *  ODE_BOUNCE         bouncing ball (closed-form checks): n=2, P=2 (g, r),
+ *                     A=6, E=1 (F0 = y1 with impact y2 <- -r y2)
+ * Accessories (Sec. 5, Sec. 6.7), all models: a0 = max y1, a1 = its time,
+ *   a2 = min y1, a3 = its time (over accepted points of one slice);
+ *   Duffing a4, a5 = y1 and t at the first detection of event 0, a6 = count
+ *   of event-0 detections; valve a4 = number of impacts; ball a4 = time of the
+ *   last impact, a5 = velocity just before it.  Initialization (Sec. 6.8)
+ *   sets a0..a5 from the state at the slice start and counts to zero. */
+enum ode_model { ODE_DUFFING = 0, ODE_KELLER_MIKSIS = 1, ODE_VALVE = 2, ODE_BOUNCE = 3 };
+
+/* Schemes (Sec. 3, Sec. 6.4): classic fixed-step RK4 and the adaptive
+ * Runge-Kutta-Cash-Karp 4(5) pair (fifth-order solution propagated). */
+enum ode_scheme { ODE_RK4 = 0, ODE_RKCK45 = 1 };
+
+/* Precision: ODE_FP64 evaluates everything in binary64.  ODE_FP32_RHS
+ * evaluates the right-hand-side stages (stage states and f) in binary32 and
+ * keeps the state, time, the state update, the embedded error estimate and
+ * norm, the step-size controller and event location in binary64.  Available
+ * for ODE_DUFFING, ODE_VALVE and ODE_BOUNCE (not for Keller-Miksis). */
+enum ode_prec { ODE_FP64 = 0, ODE_FP32_RHS = 1 };
+
+/* CopyModePossibilities of Sec. 6.3, as bit flags. */
+enum ode_copy { ODE_TIMEDOMAIN = 1, ODE_STATE = 2, ODE_PARAM = 4, ODE_ACC = 8, ODE_ALL = 15 };
+
+enum ode_ptr { ODE_PTR_HOST = 0, ODE_PTR_DEVICE = 1 };
+
+/* Time-domain update done by the Finalization hook at the end of a slice
+ * (Sec. 6.8):  KEEP leaves (t0, t1) unchanged (the next slice starts again at
+ * t0, as the Duffing Poincare loop of Sec. 7.1.1 does); T0_TO_T sets t0 to
+ * the end time (the listing of Sec. 6.8); SHIFT sets t0 to the end time and
+ * t1 = t0 + (old t1 - old t0). */
+enum ode_td_mode { ODE_TD_KEEP = 0, ODE_TD_T0_TO_T = 1, ODE_TD_SHIFT = 2 };
+
+/* Why the last slice of a system ended. */
+enum ode_sys_status {
+    ODE_ST_NONE = 0,        /* not integrated yet */
+    ODE_ST_TEND = 1,        /* reached t1 */
+    ODE_ST_EVENT_STOP = 2,  /* EventStopCondition reached (Sec. 6.6) */
+    ODE_ST_EQUILIBRIUM = 3, /* MaximumIterationForEquilibrium steps inside a zone (Sec. 4) */
+    ODE_ST_HMIN_NAN = 4,    /* non-finite step at the minimum step size (Sec. 6.5) */
+    ODE_ST_STEP_BUDGET = 5, /* per-slice step budget exhausted */
+    ODE_ST_TIMEOUT = 6      /* stopped by the launch watchdog (ode_set_time_limit) */
+};
+
+enum ode_error {
+    ODE_OK = 0,
+    ODE_ERR_INVALID_ARG = -1,
+    ODE_ERR_OUT_OF_MEMORY = -2,
+    ODE_ERR_CUDA = -3,
+    ODE_ERR_NOT_READY = -4,
+    ODE_ERR_TIMEOUT = -5,
+    ODE_ERR_UNSUPPORTED = -6
+};
+
+/* ---- solver object (Sec. 6.2) ------------------------------------------ */
+
+/* Create a solver for `n_systems` (N_T, >= 1) systems of `model`, integrated
+ * with `scheme` in precision `prec`, on CUDA device `device`.  Allocates the
+ * device arrays (time domain 2N, state nN, parameters PN, accessories AN,
+ * status, event counters EN and step counters) and zero-fills them.  The
+ * dimensions n, P, A, E are fixed by the model (Sec. 6.2's configuration).
+ * Errors: INVALID_ARG (bad enum, N < 1, FP32_RHS with Keller-Miksis),
+ * OUT_OF_MEMORY, CUDA.  *out is NULL on failure. */
+int ode_create(ode_solver **out, int model, int scheme, int prec, int n_systems, int device);
+
+/* Free the solver and its device memory (waits for its outstanding work).
+ * NULL is accepted. */
+int ode_destroy(ode_solver *s);
+
+/* Dimensions: state n (N_sys), parameters P (N_par), events E (N_E),
+ * accessories A (N_A) per system; any pointer may be NULL. */
+int ode_query_dims(const ode_solver *s, int *n_sys, int *n_par, int *n_evt, int *n_acc);
+int ode_num_systems(const ode_solver *s, int *n_systems);
+
+/* ---- properties (Sec. 6.5, 6.6) ----------------------------------------- */
+
+/* OdeProperties: per-component relative and absolute tolerances (host arrays
+ * of n doubles), maximum and minimum step, TimeStepGrowLimit and
+ * TimeStepShrinkLimit.  Defaults are those printed in Sec. 6.5: 1e-10, 1e-10,
+ * 1e6, 1e-12, 5, 0.1.  Requires 0 < h_min <= h_max < inf,
+ * 1 <= grow <= 1e4, 1e-4 <= shrink <= 1, tolerances finite and >= 0 with
+ * atol_i + rtol_i > 0.  Ignored by RK4. */
+int ode_set_tolerances(ode_solver *s, const double *rtol, const double *atol, double h_max,
+                       double h_min, double grow_limit, double shrink_limit);
+
+/* EventProperties: enable (1) or disable (0) the model's event functions; per
+ * event (host arrays of E) the direction (-1, 0, +1, MATLAB rule), the
+ * absolute tolerance of the event zone (>= 0) and the stop count (0 = never,
+ * n = stop at the n-th detection in a slice); MaximumIterationForEquilibrium
+ * (0 = off).  Arrays may be NULL when enabled = 0.  Defaults: disabled, dir
+ * -1, tol 1e-6, stop 0 (valve: stop (1, 0), equilibrium 50, Sec. 6.6). */
+int ode_set_events(ode_solver *s, int enabled, const int *direction, const double *tolerance,
+                   const int *stop_count, int max_steps_in_zone);
+
+/* Solver-wide model constants (host array, nc <= 8 doubles).  Duffing:
+ * (delta, c3, omega).  Other models take none (nc = 0). */
+int ode_set_model_constants(ode_solver *s, const double *c, int nc);
+
+/* Finalization time-domain update (enum ode_td_mode). */
+int ode_set_time_domain_mode(ode_solver *s, int mode);
+
+/* Per-slice step budget (accepted + rejected trial steps); default 1e9. */
+int ode_set_step_budget(ode_solver *s, long long max_steps_per_slice);
+
+/* Watchdog: a thread that runs longer than `seconds` within one launch stops
+ * its system with status ODE_ST_TIMEOUT and takes no further work, and the
+ * next synchronizing call (ode_synchronize, ode_run_periods with host
+ * records, ode_get_status with host arrays) returns ODE_ERR_TIMEOUT.
+ * Default 600 s; 0 disables it.  It bounds the run time of every launch. */
+int ode_set_time_limit(ode_solver *s, double seconds);
+
+/* Launch shape: block_size (multiple of 32 in [32, 1024], 0 = automatic) and
+ * persistent (1 = a persistent grid whose threads refill their slot from a
+ * device work queue the moment their system finishes; 0 = one thread per
+ * system, grid ceil(N / block_size), the launch of Sec. 6.4). */
+int ode_set_launch(ode_solver *s, int block_size, int persistent);
+
+/* ---- filling and reading the object (Sec. 6.3, 6.10) --------------------- */
+
+/* LinearSet: copy `count` consecutive systems from a pool of `pool_size`
+ * systems, pool index start_pool + i -> object index start_obj + i, for the
+ * arrays selected by copy_mode (ODE_TIMEDOMAIN: td[2][pool_size], ODE_STATE:
+ * y[n][pool_size], ODE_PARAM: p[P][pool_size], ODE_ACC: acc[A][pool_size]).
+ * Unselected arrays may be NULL.  Errors: INVALID_ARG for ranges outside
+ * [0, N) or [0, pool_size), NULL selected arrays; CUDA. */
+int ode_linear_set(ode_solver *s, int start_obj, int start_pool, int pool_size, int count,
+                   const double *td, const double *y, const double *p, const double *acc,
+                   int copy_mode, int ptr_kind, void *stream);
+
+/* RandomSet: as ode_linear_set for scattered systems: idx_obj[i] <- idx_pool[i]
+ * for i < count.  The index arrays live in the same memory kind as the data.
+ * Indices are checked on the host for ODE_PTR_HOST; device indices must be
+ * in range (out-of-range device indices are skipped by the copy kernel). */
+int ode_random_set(ode_solver *s, const int *idx_obj, const int *idx_pool, int pool_size, int count,
+                   const double *td, const double *y, const double *p, const double *acc,
+                   int copy_mode, int ptr_kind, void *stream);
+
+/* LinearGet / RandomGet: the reverse copies, object -> pool (the read-back
+ * that Sec. 6.10 does through the public h_* arrays). */
+int ode_linear_get(ode_solver *s, int start_obj, int start_pool, int pool_size, int count,
+                   double *td, double *y, double *p, double *acc, int copy_mode, int ptr_kind,
+                   void *stream);
+int ode_random_get(ode_solver *s, const int *idx_obj, const int *idx_pool, int pool_size, int count,
+                   double *td, double *y, double *p, double *acc, int copy_mode, int ptr_kind,
+                   void *stream);
+
+/* ---- integration (Sec. 6.4, Sec. 7.1.1) ---------------------------------- */
+
+/* Solve: integrate every system over its own time domain [t0, t1] once (one
+ * slice), starting with step h0 (RKCK45) or with the fixed step
+ * (t1 - t0) / ceil((t1 - t0) / h0) (RK4).  Asynchronous on `stream`.
+ * h0 > 0 required. */
+int ode_solve(ode_solver *s, double h0, void *stream);
+
+/* The iterated Solve of Sec. 7.1.1 in ONE kernel: n_transient + n_record
+ * consecutive slices per system, each slice starting with step h0 and ending
+ * with the Finalization time-domain update; after each of the last n_record
+ * slices a record of R = A + n + 1 doubles per system is written:
+ *   records[((r * R) + c) * N + i], c < A: accessories, c = A .. A+n-1: the
+ *   state at the slice end (the Poincare point), c = A + n: the end time.
+ * records may be NULL (no record written); with ODE_PTR_HOST the records are
+ * staged in a solver-owned device buffer and copied back before return.
+ * Step counters (accepted, rejected) accumulate; status and event counters
+ * describe the last slice. */
+int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, double *records,
+                    int ptr_kind, void *stream);
+
+/* Wait for all work this solver enqueued. */
+int ode_synchronize(ode_solver *s);
+
+/* Per-system results: status (N ints), accepted and rejected step counts
+ * (N long long each), event counters of the last slice (E*N ints,
+ * [event][system]).  Any pointer may be NULL.  Synchronous for host arrays. */
+int ode_get_status(ode_solver *s, int *status, long long *accepted, long long *rejected,
+                   int *event_counts, int ptr_kind, void *stream);
+
+/* Reset accepted / rejected step counters to zero. */
+int ode_reset_counters(ode_solver *s, void *stream);
+
+const char *ode_last_error(const ode_solver *s);
+
+/* ---- helpers ------------------------------------------------------------- */
+
+/* Keller-Miksis coefficients C0..C12, Eqs. (16)-(28), from physical
+ * parameters in SI units (omega in rad/s); C must hold 13 doubles.  C8 is
+ * computed as printed (with omega_1).  Pure host computation. */
+int ode_km_coefficients(double PA1, double PA2, double omega1, double omega2, double theta,
+                        double RE, double Pinf, double pV, double sigma, double mu, double rho,
+                        double cL, double gamma, double *C);
+
+/* Kernel resources of one (model, scheme, prec, persistent) instantiation:
+ * registers per thread, local (spill) bytes per thread, and the resident
+ * blocks per SM at the given block size.  Any output may be NULL. */
+int ode_kernel_info(int model, int scheme, int prec, int persistent, int block_size, int device,
+                    int *regs, int *local_bytes, int *blocks_per_sm);
+
+/* Measured FMA throughput of the device: dependent-chain DFMA and FFMA
+ * microkernels over every SM (FMA per second; one FMA = 2 flops).  Used as
+ * the roofline peak of the arithmetic-bound integrators. */
+int ode_probe_fma_peak(int device, double *dfma_per_s, double *ffma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ODEGPU_H */

@@ -1,0 +1,79 @@
+// common.cuh -- types shared by the host side of the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace odegpu {
+
+constexpr int kMaxN = 4;   // largest state dimension of a compiled model
+constexpr int kMaxP = 16;  // largest parameter count
+constexpr int kMaxA = 8;   // largest accessory count
+constexpr int kMaxE = 2;   // largest event count
+constexpr int kMaxMC = 8;  // solver-wide model constants
+
+enum Scheme { kRK4 = 0, kRKCK45 = 1 };
+enum Prec { kFP64 = 0, kFP32RHS = 1 };
+enum TdMode { kTdKeep = 0, kTdT0ToT = 1, kTdShift = 2 };
+enum SysStatus {
+  kStNone = 0,
+  kStTEnd = 1,
+  kStEventStop = 2,
+  kStEquilibrium = 3,
+  kStHminNaN = 4,
+  kStStepBudget = 5,
+  kStTimeout = 6
+};
+
+// Solver-wide settings, passed by value in the kernel parameter block (they
+// are the same for all threads: the shared per-solver properties of Sec. 6.5
+// and Sec. 6.6 of the paper).
+struct Props {
+  double rtol[kMaxN];
+  double atol[kMaxN];
+  double hmax, hmin, grow, shrink;
+  // error ratios beyond which 0.9 err^(-1/5) is clamped: (0.9/grow)^5 and
+  // (0.9/shrink)^5 (filled in by the host)
+  double err_grow, err_shrink;
+  int evt_dir[kMaxE];
+  double evt_tol[kMaxE];
+  int evt_stop[kMaxE];
+  int max_eq;
+  int events_on;
+  int td_mode;
+  long long max_steps;
+  double mc[kMaxMC];
+};
+
+// Everything one integration launch needs.  All arrays are device pointers,
+// component-major with stride N (value[c * N + i]).
+struct KArgs {
+  int N;
+  double* td;        // [2][N]  (t0, t1)
+  double* y;         // [n][N]
+  const double* p;   // [P][N]
+  double* acc;       // [A][N]
+  int* status;       // [N]
+  int* ecnt;         // [E][N]
+  long long* nacc;   // [N]  accumulated
+  long long* nrej;   // [N]  accumulated
+  double* records;   // [n_slices - n_skip][A + n + 1][N] or null
+  int n_slices;
+  int n_skip;
+  double h0;
+  unsigned int* queue_head;  // persistent launches: next system to take
+  int* flags;                // flags[0] != 0: the watchdog stopped a system
+  long long time_limit_ns;   // per-thread run-time limit of one launch (0 = none)
+  Props pr;
+};
+
+// Per-model kernel table entry: the kernel function for a (scheme,
+// precision, persistent) triple, or null when not compiled.
+typedef const void* (*KernelLookup)(int scheme, int prec, int persistent);
+
+const void* kernel_duffing(int scheme, int prec, int persistent);
+const void* kernel_keller_miksis(int scheme, int prec, int persistent);
+const void* kernel_valve(int scheme, int prec, int persistent);
+const void* kernel_bounce(int scheme, int prec, int persistent);
+
+}  // namespace odegpu

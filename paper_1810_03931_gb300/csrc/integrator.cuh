@@ -1,0 +1,574 @@
+// integrator.cuh -- the per-thread integrator kernel (one independent ODE
+// system per thread, Sec. 6.1/6.4 of the paper) for both schemes of Sec. 3,
+// with the event handling of Sec. 4 / 6.6, the accessories of Sec. 5 / 6.7 and
+// the initialization / finalization hooks of Sec. 6.8.
+//
+// GB300 design
+//  * The state of a system lives in registers for the whole launch; a launch
+//    runs many consecutive slices (the iterated Solve of Sec. 7.1.1) so the
+//    state never round-trips through HBM between slices.
+//  * Every loop iteration is ONE trial Runge-Kutta step per lane.  A lane
+//    that is locating an event (bisection in the step size, re-stepping from
+//    the last accepted point) takes its trial step through the same stage
+//    code as the lanes that take normal steps, so adaptive divergence, event
+//    location and slice / system changes of single lanes never serialise the
+//    warp's FP64 work; the bookkeeping branches are short.
+//  * The warp leaves the loop only when no lane has work (warp vote).
+//  * Persistent launches refill a lane from a device work queue (atomic
+//    counter) the moment its system finishes.
+//  * Runge-Kutta coefficients are compile-time immediates; per-solver
+//    properties come from the kernel parameter block.
+#pragma once
+
+#include "common.cuh"
+#include "models.cuh"
+
+namespace odegpu {
+
+// ---- Butcher tableaux ------------------------------------------------------
+// Cash & Karp (ACM TOMS 16, 1990), embedded 4(5) pair; the fifth-order
+// solution is propagated and E = b5 - b4 weighs the error estimate.
+namespace ck {
+constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 3.0 / 5.0, c5 = 1.0, c6 = 7.0 / 8.0;
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 3.0 / 10.0, a42 = -9.0 / 10.0, a43 = 6.0 / 5.0;
+constexpr double a51 = -11.0 / 54.0, a52 = 5.0 / 2.0, a53 = -70.0 / 27.0, a54 = 35.0 / 27.0;
+constexpr double a61 = 1631.0 / 55296.0, a62 = 175.0 / 512.0, a63 = 575.0 / 13824.0,
+                 a64 = 44275.0 / 110592.0, a65 = 253.0 / 4096.0;
+constexpr double b1 = 37.0 / 378.0, b3 = 250.0 / 621.0, b4 = 125.0 / 594.0, b6 = 512.0 / 1771.0;
+constexpr double bs1 = 2825.0 / 27648.0, bs3 = 18575.0 / 48384.0, bs4 = 13525.0 / 55296.0,
+                 bs5 = 277.0 / 14336.0, bs6 = 1.0 / 4.0;
+constexpr double e1 = b1 - bs1, e3 = b3 - bs3, e4 = b4 - bs4, e5 = 0.0 - bs5, e6 = b6 - bs6;
+}  // namespace ck
+
+template <int PREC>
+struct StageType { using type = double; };
+template <>
+struct StageType<kFP32RHS> { using type = float; };
+
+// ---- one trial step --------------------------------------------------------
+// From (t, y) with step hs and the cached first stage k1 = f(t, y), compute
+// the new state ynew and (RKCK45) the error estimate err = hs * sum e_i k_i.
+// Stage states and f are in precision T; ynew and err are binary64.
+template <class M, int SCHEME, int PREC>
+struct Stepper {
+  static constexpr int n = M::N, P = M::P;
+  using T = typename StageType<PREC>::type;
+
+  static __device__ __forceinline__ void step(double t, const double (&y)[n], double hs,
+                                              const T (&pt)[P], const T (&mct)[3],
+                                              const T (&k1)[n], double (&ynew)[n],
+                                              double (&err)[n]) {
+    T yb[n];
+#pragma unroll
+    for (int m = 0; m < n; m++) yb[m] = (T)y[m];
+    const T h = (T)hs;
+    const T tb = (T)t;
+    T ys[n];
+    if constexpr (SCHEME == kRKCK45) {
+      using namespace ck;
+      T k2[n], k3[n], k4[n], k5[n], k6[n];
+#pragma unroll
+      for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a21 * k1[m]);
+      M::template rhs<T>(tb + (T)c2 * h, ys, pt, mct, k2);
+#pragma unroll
+      for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a31 * k1[m] + (T)a32 * k2[m]);
+      M::template rhs<T>(tb + (T)c3 * h, ys, pt, mct, k3);
+#pragma unroll
+      for (int m = 0; m < n; m++)
+        ys[m] = stage(y[m], yb[m], hs, h, (T)a41 * k1[m] + (T)a42 * k2[m] + (T)a43 * k3[m]);
+      M::template rhs<T>(tb + (T)c4 * h, ys, pt, mct, k4);
+#pragma unroll
+      for (int m = 0; m < n; m++)
+        ys[m] = stage(y[m], yb[m], hs, h,
+                      (T)a51 * k1[m] + (T)a52 * k2[m] + (T)a53 * k3[m] + (T)a54 * k4[m]);
+      M::template rhs<T>(tb + (T)c5 * h, ys, pt, mct, k5);
+#pragma unroll
+      for (int m = 0; m < n; m++)
+        ys[m] = stage(y[m], yb[m], hs, h,
+                      (T)a61 * k1[m] + (T)a62 * k2[m] + (T)a63 * k3[m] + (T)a64 * k4[m] +
+                          (T)a65 * k5[m]);
+      M::template rhs<T>(tb + (T)c6 * h, ys, pt, mct, k6);
+#pragma unroll
+      for (int m = 0; m < n; m++) {
+        // binary64 state update and error estimate
+        const T sb = (T)b1 * k1[m] + (T)b3 * k3[m] + (T)b4 * k4[m] + (T)b6 * k6[m];
+        ynew[m] = y[m] + hs * (double)sb;
+        const double se = e1 * (double)k1[m] + e3 * (double)k3[m] + e4 * (double)k4[m] +
+                          e5 * (double)k5[m] + e6 * (double)k6[m];
+        err[m] = hs * se;
+      }
+    } else {
+      T k2[n], k3[n], k4[n];
+      const T half = (T)0.5;
+#pragma unroll
+      for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
+      M::template rhs<T>(tb + half * h, ys, pt, mct, k2);
+#pragma unroll
+      for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k2[m]);
+      M::template rhs<T>(tb + half * h, ys, pt, mct, k3);
+#pragma unroll
+      for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
+      M::template rhs<T>(tb + h, ys, pt, mct, k4);
+#pragma unroll
+      for (int m = 0; m < n; m++) {
+        const T sb = (T)(1.0 / 6.0) * k1[m] + (T)(1.0 / 3.0) * k2[m] + (T)(1.0 / 3.0) * k3[m] +
+                     (T)(1.0 / 6.0) * k4[m];
+        ynew[m] = y[m] + hs * (double)sb;
+        err[m] = 0.0;
+      }
+    }
+  }
+
+  // Stage state y + h * s: binary64 when T is double, binary32 otherwise.
+  static __device__ __forceinline__ T stage(double y, T yb, double hs, T h, T s) {
+    if constexpr (PREC == kFP64) {
+      (void)yb; (void)h;
+      return y + hs * s;
+    } else {
+      (void)y; (void)hs;
+      return yb + h * s;
+    }
+  }
+};
+
+// x^(-1/5) for x in [1e-6, 1e6]: a binary32 seed refined by two Newton steps
+// for z^-5 = x in binary64, z <- z + z (1 - x z^5) / 5 (each step squares the
+// relative error: ~1e-7 -> ~1e-14 -> rounding).  About a dozen binary64
+// operations instead of a general pow().
+__device__ __forceinline__ double rpow_fifth(double x) {
+  double z = (double)exp2f(-0.2f * __log2f((float)x));
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const double z2 = z * z;
+    const double r = fma(-x, z2 * z2 * z, 1.0);
+    z = fma(0.2 * z, r, z);
+  }
+  return z;
+}
+
+// Is event j crossed in its allowed direction between F_old (outside the
+// zone) and F_new?  Landing inside the zone counts (Sec. 4, MATLAB direction
+// rule of Sec. 6.6).
+__device__ __forceinline__ bool crossed(const Props& pr, int j, double F_old, double F_new) {
+  const double tol = pr.evt_tol[j];
+  const bool down = (F_old > 0.0) && (F_new <= tol);
+  const bool up = (F_old < 0.0) && (F_new >= -tol);
+  const int dir = pr.evt_dir[j];
+  return dir < 0 ? down : (dir > 0 ? up : (down || up));
+}
+
+// ---- the per-lane state machine -------------------------------------------
+template <class M, int SCHEME, int PREC>
+struct Lane {
+  static constexpr int n = M::N, P = M::P, A = M::A, E = M::E;
+  using T = typename StageType<PREC>::type;
+  using St = Stepper<M, SCHEME, PREC>;
+
+  int sys;
+  int slice;
+  int status;
+  bool k1ok;
+  bool locating;
+  int jstar;
+  int loc_it;
+  long long steps;
+  unsigned int nacc, nrej;
+  double t, t0, t1, h, hnext;
+  double y[n];
+  double p[P];
+  T pt[P];
+  T mct[3];
+  double acc[A];
+  double F[E];
+  bool leaving[E];
+  bool det[E];
+  int inzone[E];
+  int ecnt[E];
+  T k1[n];
+  double lo, hi, yhi[n];
+
+  __device__ __forceinline__ void load(const KArgs& a) {
+    const int N = a.N;
+    t0 = a.td[sys];
+    t1 = a.td[N + sys];
+#pragma unroll
+    for (int m = 0; m < n; m++) y[m] = a.y[m * N + sys];
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+      p[m] = a.p[m * N + sys];
+      pt[m] = (T)p[m];
+    }
+    slice = 0;
+    nacc = 0;
+    nrej = 0;
+  }
+
+  __device__ __forceinline__ void store(const KArgs& a) {
+    const int N = a.N;
+    a.td[sys] = t0;
+    a.td[N + sys] = t1;
+#pragma unroll
+    for (int m = 0; m < n; m++) a.y[m * N + sys] = y[m];
+#pragma unroll
+    for (int m = 0; m < A; m++) a.acc[m * N + sys] = acc[m];
+    a.status[sys] = status;
+#pragma unroll
+    for (int j = 0; j < E; j++) a.ecnt[j * N + sys] = a.pr.events_on ? ecnt[j] : 0;
+    a.nacc[sys] += nacc;
+    a.nrej[sys] += nrej;
+  }
+
+  // Start a slice: Initialization hook (Sec. 6.8), event state at t0 (a
+  // point already inside a zone is in the leaving state and is not detected,
+  // Sec. 4 / Sec. 7.2), initial step (Sec. 6.4).
+  __device__ __forceinline__ void begin_slice(const KArgs& a) {
+    const Props& pr = a.pr;
+    t = t0;
+    M::acc_init(t, y, acc);
+    if (pr.events_on) {
+      M::events(t, y, p, F);
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        leaving[j] = fabs(F[j]) <= pr.evt_tol[j];
+        inzone[j] = 0;
+        ecnt[j] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < E; j++) ecnt[j] = 0;
+    }
+    if constexpr (SCHEME == kRK4) {
+      double nsteps = ceil((t1 - t0) / a.h0 - 1e-9);
+      nsteps = nsteps < 1.0 ? 1.0 : nsteps;
+      h = (t1 - t0) / nsteps;
+    } else {
+      h = fmin(fmax(a.h0, pr.hmin), pr.hmax);
+    }
+    status = (t < t1) ? kStNone : kStTEnd;
+    steps = 0;
+    k1ok = false;
+    locating = false;
+  }
+
+  // End of a slice: Finalization time-domain update (Sec. 6.8) and record.
+  __device__ __forceinline__ void end_slice(const KArgs& a) {
+    const double t_end = t;
+    if (a.pr.td_mode == kTdT0ToT) {
+      t0 = t_end;
+    } else if (a.pr.td_mode == kTdShift) {
+      const double span = t1 - t0;
+      t0 = t_end;
+      t1 = t_end + span;
+    }
+    if (a.records != nullptr && slice >= a.n_skip) {
+      const int N = a.N;
+      constexpr int R = A + n + 1;
+      double* rec = a.records + (size_t)(slice - a.n_skip) * R * N + sys;
+#pragma unroll
+      for (int m = 0; m < A; m++) rec[(size_t)m * N] = acc[m];
+#pragma unroll
+      for (int m = 0; m < n; m++) rec[(size_t)(A + m) * N] = y[m];
+      rec[(size_t)(A + n) * N] = t_end;
+    }
+    slice++;
+  }
+
+  // Accept the point (tnew, ynew) with the detected-event flags det[]:
+  // ordinary accessories, then for each detected event in ascending order its
+  // counter, event accessories and action, then the zone bookkeeping and the
+  // stop checks (Sec. 4, 6.6, 6.7).
+  __device__ __forceinline__ void accept(const Props& pr, double tnew, const double (&ynew)[n],
+                                         bool last, bool located) {
+    t = tnew;
+#pragma unroll
+    for (int m = 0; m < n; m++) y[m] = ynew[m];
+    nacc++;
+    if constexpr (SCHEME == kRKCK45) h = hnext;
+    k1ok = false;
+    M::acc_ordinary(t, y, acc);
+    if (pr.events_on) {
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        if (det[j]) {
+          ecnt[j]++;
+          M::acc_event(j, ecnt[j], t, y, acc);
+          M::action(j, y, p);
+        }
+      }
+      M::events(t, y, p, F);
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        const bool in_zone = fabs(F[j]) <= pr.evt_tol[j];
+        if (det[j]) {
+          leaving[j] = true;
+          inzone[j] = 0;
+        } else if (leaving[j]) {
+          if (!in_zone) {
+            leaving[j] = false;
+            inzone[j] = 0;
+          } else {
+            inzone[j]++;
+            if (pr.max_eq > 0 && inzone[j] >= pr.max_eq) status = kStEquilibrium;
+          }
+        } else if (in_zone) {
+          leaving[j] = true;
+          inzone[j] = 0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < E; j++)
+        if (det[j] && pr.evt_stop[j] > 0 && ecnt[j] >= pr.evt_stop[j]) status = kStEventStop;
+    }
+    if (status == kStNone && last && !located) status = kStTEnd;
+  }
+
+  __device__ __forceinline__ void finish_location(const Props& pr) {
+    locating = false;
+    const double tnew = t + hi;
+    if (E > 1) {
+      double Fn[E];
+      M::events(tnew, yhi, p, Fn);
+#pragma unroll
+      for (int j = 0; j < E; j++)
+        if (j != jstar) det[j] = det[j] && crossed(pr, j, F[j], Fn[j]);
+    }
+    accept(pr, tnew, yhi, false, true);
+  }
+
+  // One trial step (normal or bisection).
+  __device__ __forceinline__ void trial(const KArgs& a) {
+    const Props& pr = a.pr;
+    double hs;
+    bool last = false;
+    if (locating) {
+      const double mid = 0.5 * (lo + hi);
+      if (!(mid > lo && mid < hi) || loc_it >= 200) {
+        finish_location(pr);
+        return;
+      }
+      hs = mid;
+    } else {
+      if (steps >= pr.max_steps) {
+        status = kStStepBudget;
+        return;
+      }
+      hs = h;
+      if (t1 - t <= hs * (1.0 + 1e-9)) {
+        hs = t1 - t;
+        last = true;
+      }
+    }
+    if (!k1ok) {
+      T yb[n];
+#pragma unroll
+      for (int m = 0; m < n; m++) yb[m] = (T)y[m];
+      M::template rhs<T>((T)t, yb, pt, mct, k1);
+      k1ok = true;
+    }
+    double ynew[n], err[n];
+    St::step(t, y, hs, pt, mct, k1, ynew, err);
+
+    if (locating) {
+      loc_it++;
+      double Fm[E];
+      M::events(t + hs, ynew, p, Fm);
+      const int js = jstar;
+      double fj = Fm[0];
+#pragma unroll
+      for (int j = 1; j < E; j++)
+        if (j == js) fj = Fm[j];
+      double fold = F[0], tolj = pr.evt_tol[0];
+#pragma unroll
+      for (int j = 1; j < E; j++)
+        if (j == js) { fold = F[j]; tolj = pr.evt_tol[j]; }
+      if (fabs(fj) <= tolj) {
+        hi = hs;
+#pragma unroll
+        for (int m = 0; m < n; m++) yhi[m] = ynew[m];
+        finish_location(pr);
+      } else if ((fj > 0.0) == (fold > 0.0)) {
+        lo = hs;
+      } else {
+        hi = hs;
+#pragma unroll
+        for (int m = 0; m < n; m++) yhi[m] = ynew[m];
+      }
+      return;
+    }
+
+    steps++;
+    if constexpr (SCHEME == kRKCK45) {
+      // error ratio and step-size control (Sec. 3, Sec. 6.5)
+      double errr = 0.0;
+      bool finite = true;
+#pragma unroll
+      for (int m = 0; m < n; m++) {
+        const double sc = pr.atol[m] + pr.rtol[m] * fmax(fabs(y[m]), fabs(ynew[m]));
+        const double r = fabs(err[m]) / sc;
+        errr = fmax(errr, r);
+        finite = finite && isfinite(r) && isfinite(ynew[m]);
+      }
+      const bool at_min = hs <= pr.hmin;
+      if (!finite) {
+        nrej++;
+        if (at_min) status = kStHminNaN;
+        else h = fmax(pr.shrink * hs, pr.hmin);
+        return;
+      }
+      // new step factor 0.9 err^(-1/5), clamped to [shrink, grow]
+      double fac;
+      if (errr <= pr.err_grow) {
+        fac = pr.grow;
+      } else if (errr >= pr.err_shrink) {
+        fac = pr.shrink;
+      } else {
+        fac = fmin(fmax(0.9 * rpow_fifth(errr), pr.shrink), pr.grow);
+      }
+      if (errr > 1.0 && !at_min) {
+        nrej++;
+        h = fmin(fmax(hs * fac, pr.hmin), pr.hmax);
+        return;
+      }
+      hnext = fmin(fmax(hs * fac, pr.hmin), pr.hmax);
+    } else {
+      bool finite = true;
+#pragma unroll
+      for (int m = 0; m < n; m++) finite = finite && isfinite(ynew[m]);
+      if (!finite) {
+        nrej++;
+        status = kStHminNaN;
+        return;
+      }
+    }
+
+    const double tnew = last ? t1 : t + hs;
+#pragma unroll
+    for (int j = 0; j < E; j++) det[j] = false;
+    if (pr.events_on) {
+      double Fn[E];
+      M::events(tnew, ynew, p, Fn);
+      int js = -1;
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        if (!leaving[j] && crossed(pr, j, F[j], Fn[j])) {
+          det[j] = true;
+          js = j;
+        }
+      }
+      if (js >= 0) {
+        double fj = Fn[0], tolj = pr.evt_tol[0];
+#pragma unroll
+        for (int j = 1; j < E; j++)
+          if (j == js) { fj = Fn[j]; tolj = pr.evt_tol[j]; }
+        if (fabs(fj) > tolj) {
+          // configuration a of Sec. 4: the step jumped over the zone --
+          // locate by bisection in the step size from (t, y)
+          locating = true;
+          jstar = js;
+          loc_it = 0;
+          lo = 0.0;
+          hi = hs;
+#pragma unroll
+          for (int m = 0; m < n; m++) yhi[m] = ynew[m];
+          return;
+        }
+      }
+    }
+    accept(pr, tnew, ynew, last, false);
+  }
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- the kernel --------------------------------------------------------------
+template <class M, int SCHEME, int PREC, bool PERSIST>
+__global__ void __launch_bounds__(256) ode_kernel(const KArgs a) {
+  using L_t = Lane<M, SCHEME, PREC>;
+  using T = typename L_t::T;
+  L_t L;
+#pragma unroll
+  for (int m = 0; m < 3; m++) L.mct[m] = (T)a.pr.mc[m];
+
+  bool active;
+  if constexpr (PERSIST) {
+    L.sys = (int)atomicAdd(a.queue_head, 1u);
+  } else {
+    L.sys = blockIdx.x * blockDim.x + threadIdx.x;
+  }
+  active = L.sys < a.N;
+  bool fresh = active;  // a new system is loaded and its slice must begin
+
+  // Resolve slice / system ends (also zero-length slices) until the lane has
+  // a slice to integrate or no work at all.
+  auto settle = [&]() {
+    while (active) {
+      if (fresh) {
+        L.load(a);
+        L.begin_slice(a);
+        fresh = false;
+      }
+      if (L.status == kStNone) return;
+      L.end_slice(a);
+      if (L.slice < a.n_slices) {
+        L.begin_slice(a);
+        continue;
+      }
+      L.store(a);
+      if constexpr (PERSIST) {
+        L.sys = (int)atomicAdd(a.queue_head, 1u);
+        active = L.sys < a.N;
+        fresh = active;
+      } else {
+        active = false;
+      }
+    }
+  };
+
+  // Watchdog: a thread that has run longer than time_limit_ns stops its
+  // system with kStTimeout, raises flags[0] and takes no further work, so no
+  // launch can run unbounded (e.g. a system crawling at the minimum step).
+  const unsigned long long t_start = globaltimer_ns();
+  unsigned int wd = 0;
+  settle();
+  while (__any_sync(0xffffffffu, active)) {
+    if (active) {
+      L.trial(a);
+      if (L.status != kStNone) settle();
+      if (active && a.time_limit_ns > 0 && ((++wd & 1023u) == 0u) &&
+          globaltimer_ns() - t_start > (unsigned long long)a.time_limit_ns) {
+        L.status = kStTimeout;
+        L.store(a);
+        atomicExch(a.flags, 1);
+        active = false;
+      }
+    }
+  }
+}
+
+// Kernel lookup for one model: every (scheme, precision, persistent) variant.
+template <class M>
+const void* lookup_kernel(int scheme, int prec, int persistent) {
+  if (prec == kFP64) {
+    if (scheme == kRK4)
+      return persistent ? (const void*)ode_kernel<M, kRK4, kFP64, true>
+                        : (const void*)ode_kernel<M, kRK4, kFP64, false>;
+    return persistent ? (const void*)ode_kernel<M, kRKCK45, kFP64, true>
+                      : (const void*)ode_kernel<M, kRKCK45, kFP64, false>;
+  }
+  if constexpr (M::kHasFP32) {
+    if (scheme == kRK4)
+      return persistent ? (const void*)ode_kernel<M, kRK4, kFP32RHS, true>
+                        : (const void*)ode_kernel<M, kRK4, kFP32RHS, false>;
+    return persistent ? (const void*)ode_kernel<M, kRKCK45, kFP32RHS, true>
+                      : (const void*)ode_kernel<M, kRKCK45, kFP32RHS, false>;
+  }
+  return nullptr;
+}
+
+}  // namespace odegpu

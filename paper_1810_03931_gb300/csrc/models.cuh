@@ -1,0 +1,179 @@
+// models.cuh -- the pre-declared device hooks of the paper (Sec. 6.5-6.8) for
+// each compiled model: right-hand side, event functions, event action,
+// accessories and initialization.  They are inlined into the integrator
+// kernels of the same translation unit (Sec. 6.9: hooks compiled in a
+// separate module cost about 14% on the paper's hardware).
+//
+// Template parameter T of rhs() is the stage precision: double, or float for
+// the FP32 right-hand-side form.
+#pragma once
+
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace odegpu {
+
+__device__ __forceinline__ float cos_t(float x) { return cosf(x); }
+__device__ __forceinline__ double cos_t(double x) { return cos(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+
+// Ordinary accessories shared by all models (Sec. 6.7): running maximum and
+// minimum of y1 over accepted points, with their times.
+__device__ __forceinline__ void acc_minmax(double t, double y1, double* a) {
+  if (y1 > a[0]) { a[0] = y1; a[1] = t; }
+  if (y1 < a[2]) { a[2] = y1; a[3] = t; }
+}
+
+// --------------------------------------------------------------------------
+// Duffing oscillator, Eqs. (1)-(2):
+//   y1' = y2,  y2' = delta y1 - c3 y1^3 - k y2 + B cos(omega t)
+// p = (k, B); model constants mc = (delta, c3, omega).
+// Event 0: F = y2 (extrema of y1).  Accessories a0..a3 min/max, a4/a5 the
+// first detected event-0 point, a6 its detection count.
+// --------------------------------------------------------------------------
+struct Duffing {
+  static constexpr int N = 2, P = 2, A = 7, E = 1;
+  static constexpr bool kHasFP32 = true;
+
+  template <class T>
+  static __device__ __forceinline__ void rhs(T t, const T (&y)[N], const T (&p)[P],
+                                             const T (&mc)[3], T (&f)[N]) {
+    f[0] = y[1];
+    f[1] = mc[0] * y[0] - mc[1] * (y[0] * y[0] * y[0]) - p[0] * y[1] + p[1] * cos_t(mc[2] * t);
+  }
+  static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
+                                                double (&F)[E]) {
+    F[0] = y[1];
+  }
+  static __device__ __forceinline__ void action(int, double (&)[N], const double (&)[P]) {}
+  static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
+    a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = y[0]; a[5] = t; a[6] = 0.0;
+  }
+  static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
+    acc_minmax(t, y[0], a);
+  }
+  static __device__ __forceinline__ void acc_event(int j, int cnt, double t, const double (&y)[N],
+                                                   double (&a)[A]) {
+    if (j == 0) {
+      a[6] = (double)cnt;
+      if (cnt == 1) { a[4] = y[0]; a[5] = t; }
+    }
+  }
+};
+
+// --------------------------------------------------------------------------
+// Keller-Miksis bubble, dimensionless form Eqs. (12)-(15) with the
+// coefficients C0..C12 of Eqs. (16)-(28) as per-system parameters; t is the
+// dimensionless time tau (periods of the first excitation).
+// Event 0: F = y2.  Accessories a0..a3 min/max of y1 with times.
+// --------------------------------------------------------------------------
+struct KellerMiksis {
+  static constexpr int N = 2, P = 13, A = 4, E = 1;
+  static constexpr bool kHasFP32 = false;
+
+  template <class T>
+  static __device__ __forceinline__ void rhs(T tau, const T (&y)[N], const T (&C)[P],
+                                             const T (&)[3], T (&f)[N]) {
+    const double y1 = y[0], y2 = y[1];
+    const double rx = 1.0 / y1;
+    double s1, c1;
+    sincospi(2.0 * tau, &s1, &c1);  // sin, cos of 2 pi tau
+    double s2 = 0.0, c2 = 0.0;
+    if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * tau + C[12], &s2, &c2);
+    const double one_c9y2 = 1.0 + C[9] * y2;
+    const double num = (C[0] + C[1] * y2) * pow(rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
+                       C[4] * y2 * rx - (1.0 - C[9] * y2 * (1.0 / 3.0)) * 1.5 * y2 * y2 -
+                       (C[5] * s1 + C[6] * s2) * one_c9y2 - y1 * (C[7] * c1 + C[8] * c2);
+    const double den = y1 - C[9] * y1 * y2 + C[4] * C[9];
+    f[0] = y2;
+    f[1] = num / den;
+  }
+  static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
+                                                double (&F)[E]) {
+    F[0] = y[1];
+  }
+  static __device__ __forceinline__ void action(int, double (&)[N], const double (&)[P]) {}
+  static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
+    a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t;
+  }
+  static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
+    acc_minmax(t, y[0], a);
+  }
+  static __device__ __forceinline__ void acc_event(int, int, double, const double (&)[N], double (&)[A]) {}
+};
+
+// --------------------------------------------------------------------------
+// Pressure relief valve, Eqs. (29)-(31), impact law Eqs. (32)-(34);
+// p = (kappa, delta, beta, q, r).  Event 0: F = y2 (maxima of the
+// displacement, the Poincare section of Sec. 7.3); event 1: F = y1 (contact
+// with the seat), whose action is y2 <- -r y2.  Accessories a0..a3 min/max
+// of y1 with times, a4 the number of impacts.
+// --------------------------------------------------------------------------
+struct Valve {
+  static constexpr int N = 3, P = 5, A = 5, E = 2;
+  static constexpr bool kHasFP32 = true;
+
+  template <class T>
+  static __device__ __forceinline__ void rhs(T, const T (&y)[N], const T (&p)[P], const T (&)[3],
+                                             T (&f)[N]) {
+    f[0] = y[1];
+    f[1] = -p[0] * y[1] - (y[0] + p[1]) + y[2];
+    f[2] = p[2] * (p[3] - y[0] * sqrt_t(y[2]));
+  }
+  static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
+                                                double (&F)[E]) {
+    F[0] = y[1];
+    F[1] = y[0];
+  }
+  static __device__ __forceinline__ void action(int j, double (&y)[N], const double (&p)[P]) {
+    if (j == 1) y[1] = -p[4] * y[1];
+  }
+  static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
+    a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = 0.0;
+  }
+  static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
+    acc_minmax(t, y[0], a);
+  }
+  static __device__ __forceinline__ void acc_event(int j, int cnt, double, const double (&)[N],
+                                                   double (&a)[A]) {
+    if (j == 1) a[4] = (double)cnt;
+  }
+};
+
+// --------------------------------------------------------------------------
+// Bouncing ball: y1' = y2, y2' = -g, p = (g, r); event 0: F = y1 with the
+// impact y2 <- -r y2.  Accessories a0..a3 min/max with times, a4 the time of
+// the last impact, a5 the velocity just before it.
+// --------------------------------------------------------------------------
+struct Bounce {
+  static constexpr int N = 2, P = 2, A = 6, E = 1;
+  static constexpr bool kHasFP32 = true;
+
+  template <class T>
+  static __device__ __forceinline__ void rhs(T, const T (&y)[N], const T (&p)[P], const T (&)[3],
+                                             T (&f)[N]) {
+    f[0] = y[1];
+    f[1] = -p[0];
+  }
+  static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
+                                                double (&F)[E]) {
+    F[0] = y[0];
+  }
+  static __device__ __forceinline__ void action(int j, double (&y)[N], const double (&p)[P]) {
+    if (j == 0) y[1] = -p[1] * y[1];
+  }
+  static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
+    a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = t; a[5] = y[1];
+  }
+  static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
+    acc_minmax(t, y[0], a);
+  }
+  static __device__ __forceinline__ void acc_event(int j, int, double t, const double (&y)[N],
+                                                   double (&a)[A]) {
+    if (j == 0) { a[4] = t; a[5] = y[1]; }
+  }
+};
+
+}  // namespace odegpu

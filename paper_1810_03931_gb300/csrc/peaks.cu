@@ -1,0 +1,62 @@
+// peaks.cu -- FMA throughput probes: the roofline denominator of the
+// arithmetic-bound integrators (binary64 and binary32 CUDA-core FMA rates).
+// Eight independent dependent chains per thread, every SM filled.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/odegpu.h"
+
+namespace {
+
+template <typename T>
+__global__ void fma_chains(T* out, int iters, T a, T b) {
+  T x0 = (T)threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+template <typename T>
+cudaError_t time_chains(int sms, int iters, double* fma_per_s) {
+  const int threads = 256, blocks = sms * 4;
+  T* out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(T));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fma_chains<T><<<blocks, threads>>>(out, 8, (T)1.0000001, (T)1e-9);  // warm-up
+  cudaEventRecord(e0);
+  fma_chains<T><<<blocks, threads>>>(out, iters, (T)1.0000001, (T)1e-9);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) *fma_per_s = (double)blocks * threads * iters * 16 * 8 / (ms * 1e-3);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return e;
+}
+
+}  // namespace
+
+extern "C" int ode_probe_fma_peak(int device, double* dfma_per_s, double* ffma_per_s) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return ODE_ERR_CUDA;
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess && dfma_per_s) e = time_chains<double>(sms, 1000, dfma_per_s);
+  if (e == cudaSuccess && ffma_per_s) e = time_chains<float>(sms, 20000, ffma_per_s);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? ODE_OK : ODE_ERR_CUDA;
+}

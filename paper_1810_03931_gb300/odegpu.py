@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the C ABI in ``include/odegpu.h`` (same names).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``libodegpu.so``.  Arrays may be numpy arrays (host memory) or torch tensors
+(host or CUDA; CUDA tensors are passed as device pointers).  A missing or
+unloadable library raises ``ODEError``; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# enums of include/odegpu.h
+ODE_DUFFING, ODE_KELLER_MIKSIS, ODE_VALVE, ODE_BOUNCE = 0, 1, 2, 3
+ODE_RK4, ODE_RKCK45 = 0, 1
+ODE_FP64, ODE_FP32_RHS = 0, 1
+ODE_TIMEDOMAIN, ODE_STATE, ODE_PARAM, ODE_ACC, ODE_ALL = 1, 2, 4, 8, 15
+ODE_PTR_HOST, ODE_PTR_DEVICE = 0, 1
+ODE_TD_KEEP, ODE_TD_T0_TO_T, ODE_TD_SHIFT = 0, 1, 2
+(ODE_ST_NONE, ODE_ST_TEND, ODE_ST_EVENT_STOP, ODE_ST_EQUILIBRIUM, ODE_ST_HMIN_NAN,
+ ODE_ST_STEP_BUDGET, ODE_ST_TIMEOUT) = range(7)
+ODE_OK, ODE_ERR_INVALID_ARG, ODE_ERR_OUT_OF_MEMORY, ODE_ERR_CUDA = 0, -1, -2, -3
+ODE_ERR_NOT_READY, ODE_ERR_TIMEOUT, ODE_ERR_UNSUPPORTED = -4, -5, -6
+
+# exported symbols, in the order of the header
+SYMBOLS = (
+    "ode_create", "ode_destroy", "ode_query_dims", "ode_num_systems", "ode_set_tolerances",
+    "ode_set_events", "ode_set_model_constants", "ode_set_time_domain_mode", "ode_set_step_budget",
+    "ode_set_time_limit", "ode_set_launch", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
+    "ode_solve", "ode_run_periods", "ode_synchronize", "ode_get_status", "ode_reset_counters",
+    "ode_last_error", "ode_km_coefficients", "ode_kernel_info", "ode_probe_fma_peak",
+)
+
+
+class ODEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("odegpu error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_longlong)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libodegpu.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ODEError(ODE_ERR_UNSUPPORTED, "libodegpu.so is not built (run build())")
+    L = ctypes.CDLL(_build.LIB)
+    i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "ode_create": [ctypes.POINTER(_vp), i, i, i, i, i],
+        "ode_destroy": [_vp],
+        "ode_query_dims": [_vp, _ip, _ip, _ip, _ip],
+        "ode_num_systems": [_vp, _ip],
+        "ode_set_tolerances": [_vp, _dp, _dp, d, d, d, d],
+        "ode_set_events": [_vp, i, _ip, _dp, _ip, i],
+        "ode_set_model_constants": [_vp, _dp, i],
+        "ode_set_time_domain_mode": [_vp, i],
+        "ode_set_step_budget": [_vp, ll],
+        "ode_set_time_limit": [_vp, d],
+        "ode_set_launch": [_vp, i, i],
+        "ode_linear_set": [_vp, i, i, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
+        "ode_random_set": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
+        "ode_linear_get": [_vp, i, i, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
+        "ode_random_get": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
+        "ode_solve": [_vp, d, _vp],
+        "ode_run_periods": [_vp, d, i, i, _vp, i, _vp],
+        "ode_synchronize": [_vp],
+        "ode_get_status": [_vp, _vp, _vp, _vp, _vp, i, _vp],
+        "ode_reset_counters": [_vp, _vp],
+        "ode_last_error": [_vp],
+        "ode_km_coefficients": [d] * 13 + [_dp],
+        "ode_kernel_info": [i, i, i, i, i, i, _ip, _ip, _ip],
+        "ode_probe_fma_peak": [i, _dp, _dp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "ode_last_error" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def ode_last_error(s=None) -> str:
+    msg = load().ode_last_error(s)
+    return msg.decode() if msg else ""
+
+
+def _check(rc, s=None):
+    if rc != ODE_OK:
+        raise ODEError(rc, ode_last_error(s))
+    return rc
+
+
+# ---- array marshalling ---------------------------------------------------------
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _arr(x, dtype):
+    """(pointer as int or None, ptr_kind or None) for numpy / torch arrays."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        want = torch.float64 if dtype == np.float64 else (torch.int32 if dtype == np.int32 else torch.int64)
+        if x.dtype != want or not x.is_contiguous():
+            raise ODEError(ODE_ERR_INVALID_ARG, "tensor must be contiguous %s" % want)
+        return x.data_ptr(), (ODE_PTR_DEVICE if x.is_cuda else ODE_PTR_HOST)
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise ODEError(ODE_ERR_INVALID_ARG, "array must be a C-contiguous numpy %s array" % np.dtype(dtype))
+    return x.ctypes.data, ODE_PTR_HOST
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ODEError(ODE_ERR_INVALID_ARG, "mixing host and device arrays in one call")
+    return ks.pop() if ks else ODE_PTR_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+# ---- C ABI, same names -----------------------------------------------------------
+def ode_create(model, scheme, prec, n_systems, device=0):
+    h = _vp()
+    _check(load().ode_create(ctypes.byref(h), model, scheme, prec, n_systems, device))
+    return h
+
+
+def ode_destroy(s):
+    return _check(load().ode_destroy(s))
+
+
+def ode_query_dims(s):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().ode_query_dims(s, *[ctypes.byref(x) for x in v]), s)
+    return tuple(x.value for x in v)  # (n, P, E, A)
+
+
+def ode_num_systems(s):
+    v = ctypes.c_int()
+    _check(load().ode_num_systems(s, ctypes.byref(v)), s)
+    return v.value
+
+
+def ode_set_tolerances(s, rtol, atol, h_max, h_min, grow_limit, shrink_limit):
+    r = np.ascontiguousarray(rtol, dtype=np.float64)
+    a = np.ascontiguousarray(atol, dtype=np.float64)
+    return _check(load().ode_set_tolerances(s, r.ctypes.data_as(_dp), a.ctypes.data_as(_dp),
+                                            h_max, h_min, grow_limit, shrink_limit), s)
+
+
+def ode_set_events(s, enabled, direction=None, tolerance=None, stop_count=None, max_steps_in_zone=0):
+    d = None if direction is None else np.ascontiguousarray(direction, dtype=np.int32)
+    t = None if tolerance is None else np.ascontiguousarray(tolerance, dtype=np.float64)
+    c = None if stop_count is None else np.ascontiguousarray(stop_count, dtype=np.int32)
+    return _check(load().ode_set_events(
+        s, int(enabled), None if d is None else d.ctypes.data_as(_ip),
+        None if t is None else t.ctypes.data_as(_dp), None if c is None else c.ctypes.data_as(_ip),
+        int(max_steps_in_zone)), s)
+
+
+def ode_set_model_constants(s, c):
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    return _check(load().ode_set_model_constants(s, c.ctypes.data_as(_dp), c.size), s)
+
+
+def ode_set_time_domain_mode(s, mode):
+    return _check(load().ode_set_time_domain_mode(s, mode), s)
+
+
+def ode_set_step_budget(s, max_steps):
+    return _check(load().ode_set_step_budget(s, int(max_steps)), s)
+
+
+def ode_set_time_limit(s, seconds):
+    return _check(load().ode_set_time_limit(s, float(seconds)), s)
+
+
+def ode_set_launch(s, block_size=0, persistent=0):
+    return _check(load().ode_set_launch(s, int(block_size), int(persistent)), s)
+
+
+def _copy(fn, s, a0, a1, pool_size, count, td, y, p, acc, copy_mode, stream, idx=False):
+    ptrs = [_arr(x, np.float64) for x in (td, y, p, acc)]
+    if idx:
+        i0, k0 = _arr(a0, np.int32)
+        i1, k1 = _arr(a1, np.int32)
+        kind = _kind(k0, k1, *[k for _, k in ptrs])
+        a0, a1 = i0, i1
+    else:
+        kind = _kind(*[k for _, k in ptrs])
+    return _check(fn(s, a0, a1, pool_size, count, *[pp for pp, _ in ptrs], copy_mode, kind,
+                     _stream(stream)), s)
+
+
+def ode_linear_set(s, start_obj, start_pool, pool_size, count, td=None, y=None, p=None, acc=None,
+                   copy_mode=ODE_ALL, stream=None):
+    return _copy(load().ode_linear_set, s, start_obj, start_pool, pool_size, count, td, y, p, acc,
+                 copy_mode, stream)
+
+
+def ode_linear_get(s, start_obj, start_pool, pool_size, count, td=None, y=None, p=None, acc=None,
+                   copy_mode=ODE_ALL, stream=None):
+    return _copy(load().ode_linear_get, s, start_obj, start_pool, pool_size, count, td, y, p, acc,
+                 copy_mode, stream)
+
+
+def ode_random_set(s, idx_obj, idx_pool, pool_size, count, td=None, y=None, p=None, acc=None,
+                   copy_mode=ODE_ALL, stream=None):
+    return _copy(load().ode_random_set, s, idx_obj, idx_pool, pool_size, count, td, y, p, acc,
+                 copy_mode, stream, idx=True)
+
+
+def ode_random_get(s, idx_obj, idx_pool, pool_size, count, td=None, y=None, p=None, acc=None,
+                   copy_mode=ODE_ALL, stream=None):
+    return _copy(load().ode_random_get, s, idx_obj, idx_pool, pool_size, count, td, y, p, acc,
+                 copy_mode, stream, idx=True)
+
+
+def ode_solve(s, h0, stream=None):
+    return _check(load().ode_solve(s, h0, _stream(stream)), s)
+
+
+def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
+    ptr, kind = _arr(records, np.float64)
+    return _check(load().ode_run_periods(s, h0, n_transient, n_record, ptr,
+                                         ODE_PTR_HOST if kind is None else kind, _stream(stream)), s)
+
+
+def ode_synchronize(s):
+    return _check(load().ode_synchronize(s), s)
+
+
+def ode_get_status(s, status=None, accepted=None, rejected=None, event_counts=None, stream=None):
+    a = _arr(status, np.int32)
+    b = _arr(accepted, np.int64)
+    c = _arr(rejected, np.int64)
+    d = _arr(event_counts, np.int32)
+    kind = _kind(a[1], b[1], c[1], d[1])
+    return _check(load().ode_get_status(s, a[0], b[0], c[0], d[0], kind, _stream(stream)), s)
+
+
+def ode_reset_counters(s, stream=None):
+    return _check(load().ode_reset_counters(s, _stream(stream)), s)
+
+
+def ode_km_coefficients(PA1, PA2, omega1, omega2, theta, RE, Pinf, pV, sigma, mu, rho, cL, gamma):
+    C = np.zeros(13)
+    _check(load().ode_km_coefficients(PA1, PA2, omega1, omega2, theta, RE, Pinf, pV, sigma, mu, rho,
+                                      cL, gamma, C.ctypes.data_as(_dp)))
+    return C
+
+
+def ode_kernel_info(model, scheme, prec, persistent=0, block_size=0, device=0):
+    r, l, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().ode_kernel_info(model, scheme, prec, persistent, block_size, device, ctypes.byref(r),
+                                  ctypes.byref(l), ctypes.byref(b)))
+    return dict(regs=r.value, local_bytes=l.value, blocks_per_sm=b.value)
+
+
+def ode_probe_fma_peak(device=0):
+    d, f = ctypes.c_double(), ctypes.c_double()
+    _check(load().ode_probe_fma_peak(device, ctypes.byref(d), ctypes.byref(f)))
+    return d.value, f.value

@@ -1,0 +1,92 @@
+"""Host-side checks of the native library that need no GPU: it builds for
+sm_103a, loads, exports every symbol that include/odegpu.h declares, and its
+pure host helpers agree with the oracle's independent implementations."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_1810_03931_gb300 import build as B
+from paper_1810_03931_gb300 import odegpu as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "odegpu.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*\**(ode_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = B.build()
+    assert os.path.exists(lib)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (ode_\w+)$", out, re.M))
+    declared = _header_symbols()
+    assert len(declared) >= 20
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    assert set(G.SYMBOLS) == set(declared)
+    L = G.load()
+    for s in declared:
+        assert hasattr(L, s)
+
+
+def test_kernels_are_compiled_for_sm_103a():
+    objdir = B.BUILD
+    assert any(f.startswith("kern_") for f in os.listdir(objdir))
+    assert any(f == "-gencode" for f in B.NVCC_FLAGS)
+    assert "arch=compute_103a,code=sm_103a" in B.NVCC_FLAGS
+
+
+def test_create_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(G.ODEError) as e:
+        G.ode_create(G.ODE_DUFFING, G.ODE_RKCK45, G.ODE_FP64, 16, 0)
+    assert e.value.code in (G.ODE_ERR_CUDA, G.ODE_ERR_INVALID_ARG)
+    assert G.ode_last_error()
+
+
+def test_argument_validation_before_any_device_work():
+    with pytest.raises(G.ODEError) as e:
+        G.ode_create(9, 0, 0, 16, 0)
+    assert e.value.code == G.ODE_ERR_INVALID_ARG
+    with pytest.raises(G.ODEError) as e:
+        G.ode_create(G.ODE_KELLER_MIKSIS, 1, G.ODE_FP32_RHS, 16, 0)
+    assert e.value.code == G.ODE_ERR_INVALID_ARG
+    with pytest.raises(G.ODEError) as e:
+        G.ode_create(G.ODE_DUFFING, 1, 0, 0, 0)
+    assert e.value.code == G.ODE_ERR_INVALID_ARG
+
+
+def test_km_coefficients_agree_with_the_oracle():
+    """Two independent codings of Eqs. (16)-(28)."""
+    w = W.keller_miksis(7, 5, 0, 1)
+    ph = w["phys"]
+    ref = O.km_coefficients(w["PA"], w["omega"], PA2=0.3e5, omega2=2 * w["omega"], theta=0.4, **ph)
+    for i in range(w["N"]):
+        c = G.ode_km_coefficients(w["PA"][i], 0.3e5, w["omega"][i], 2 * w["omega"][i], 0.4, ph["RE"],
+                                  ph["Pinf"], ph["pV"], ph["sigma"], ph["mu"], ph["rho"], ph["cL"],
+                                  ph["gamma"])
+        np.testing.assert_allclose(c, ref[:, i], rtol=1e-14, atol=0)
+
+
+def test_workload_generators_are_seeded_and_shaped():
+    a = W.duffing_rkck()
+    assert a["N"] == 2 ** 17 and a["p"].shape == (2, 2 ** 17)
+    assert a["p"][0, 1] > a["p"][0, 0] and a["p"][1, 511] == a["p"][1, 0]  # k fastest
+    k = W.keller_miksis()
+    assert k["N"] == 2 ** 18
+    v = W.valve()
+    assert v["N"] == 2 ** 16 and v["p"][3, 0] == 0.2 and v["p"][3, -1] == 10.0
+    s1, s2 = W.serving_mix(50), W.serving_mix(50)
+    assert s1 == s2
+    assert all(1 <= r["size"] <= 2 ** 16 and 16 <= r["horizon"] <= 1024 for r in s1)
+    idx = W.sample_indices(1000, 20, corners=(0, 999))
+    assert len(idx) == 20 and 0 in idx and 999 in idx

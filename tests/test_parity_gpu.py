@@ -1,0 +1,391 @@
+"""GPU (CUDA library, through the C ABI) against the CPU oracle, element by
+element on the same seeded inputs.
+
+Acceptance:
+  * RK4 binary64 final states and records: 1e-12 relative (atol 1e-12).
+  * RKCK45 accessories, event points and Poincare points: 100 x rtol on
+    non-chaotic parameter points.  A point is non-chaotic when the oracle at
+    rtol and at rtol / 10 agrees on its recorded continuous quantities (end
+    state and event-located maxima) within 10 x rtol.
+  * Discrete accessories (max / min over accepted points) may pick the other
+    of two near-equal samples; their times are then checked for validity
+    (the value agrees) instead of equality.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_1810_03931_gb300 import odegpu as G
+
+from _runners import DIMS, gpu_load, gpu_results, gpu_solver, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def _rel_close(a, b, rtol, atol):
+    return np.abs(a - b) <= atol + rtol * np.abs(b)
+
+
+def _nonchaotic(w, n_tr, n_rec, cont_rows, rtol):
+    """Mask of systems whose continuous records agree at rtol and rtol/10."""
+    r1 = run_oracle(w, NTHREADS, n_transient=n_tr, n_record=n_rec)
+    r2 = run_oracle(w, NTHREADS, n_transient=n_tr, n_record=n_rec, rtol=rtol / 10, atol=rtol / 10)
+    ok = np.ones(w["N"], dtype=bool)
+    for row in cont_rows:
+        ok &= np.all(_rel_close(r1["records"][:, row], r2["records"][:, row], 10 * rtol, 10 * rtol), axis=0)
+    return ok, r1
+
+
+def _compare_records(g, o, mask, A, n, tol, discrete_pairs=((0, 1), (2, 3)), exact_rows=()):
+    """Compare records of `mask` systems; returns the number compared."""
+    rg, ro = g["records"][:, :, mask], o["records"][:, :, mask]
+    R = A + n + 1
+    for row in range(R):
+        if row in exact_rows:
+            np.testing.assert_array_equal(rg[:, row], ro[:, row], err_msg="row %d" % row)
+            continue
+        times = {t for _, t in discrete_pairs}
+        if row in times:
+            continue
+        np.testing.assert_array_less(np.abs(rg[:, row] - ro[:, row]), tol * (1 + np.abs(ro[:, row])),
+                                     err_msg="record row %d" % row)
+    for vrow, trow in discrete_pairs:
+        same_t = np.abs(rg[:, trow] - ro[:, trow]) <= tol * (1 + np.abs(ro[:, trow]))
+        same_v = np.abs(rg[:, vrow] - ro[:, vrow]) <= tol * (1 + np.abs(ro[:, vrow]))
+        # a different time is valid only when the sampled values tie
+        assert np.all(same_t | same_v)
+    return int(mask.sum())
+
+
+# ---------------------------------------------------------------------------
+# Duffing RK4 (the Poincare loop of Sec. 7.1.1 with accessories), full size.
+# ---------------------------------------------------------------------------
+def test_duffing_rk4_full_size_parity():
+    w = W.duffing_rk4()
+    g = run_gpu(w)
+    o = run_oracle(w, NTHREADS)
+    assert np.all(g["status"] == W.RK4 + 1) and np.all(o["status"] == 1)
+    np.testing.assert_array_equal(g["nacc"], o["nacc"])
+    np.testing.assert_array_equal(g["nacc"], 96 * 1000)
+    assert np.all(_rel_close(g["y"], o["y"], 1e-12, 1e-12))
+    rg, ro = g["records"], o["records"]
+    for row in (0, 2, 4, 7, 8):  # max, min, event-acc init value, Poincare point
+        assert np.all(_rel_close(rg[:, row], ro[:, row], 1e-12, 1e-12)), row
+    np.testing.assert_array_equal(rg[:, 9], ro[:, 9])  # end time: t1 exactly
+    for vrow, trow in ((0, 1), (2, 3)):
+        same_t = rg[:, trow] == ro[:, trow]
+        assert np.all(same_t | _rel_close(rg[:, vrow], ro[:, vrow], 1e-12, 1e-12))
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_duffing_rk4_launch_forms_identical(persistent):
+    w = W.duffing_rk4(N=333, n_transient=2, n_record=2)
+    base = run_gpu(w, persistent=0, block=64)
+    other = run_gpu(w, persistent=persistent, block=128)
+    for key in ("y", "acc", "records", "nacc"):
+        np.testing.assert_array_equal(base[key], other[key])
+
+
+# ---------------------------------------------------------------------------
+# Duffing RKCK45 with the local-maximum event (Sec. 7.1.2), cfg of the bench.
+# ---------------------------------------------------------------------------
+def _duffing_rkck_small(nk=32, nB=16, n_tr=20, n_rec=8):
+    w = W.duffing_rkck(nk, nB, n_tr, n_rec)
+    return w
+
+
+def test_duffing_rkck_event_parity_grid():
+    w = _duffing_rkck_small()
+    A, n = 7, 2
+    mask, o = _nonchaotic(w, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
+    assert mask.mean() > 0.5
+    g = run_gpu(w)
+    assert np.all(g["status"] == 1)
+    # event counts are integers: compared exactly on non-chaotic points
+    cnt = _compare_records(g, o, mask, A, n, tol=1e-8, exact_rows=(6, 9))
+    assert cnt > 0
+    # step counts agree closely (the step-size sequences are the same up to
+    # rounding of the error estimate)
+    ratio = g["nacc"][mask] / o["nacc"][mask]
+    assert np.all(np.abs(ratio - 1) < 1e-3)
+
+
+def test_duffing_rkck_full_size_sampled():
+    """The bench workload at full size (2^17 systems, 1024 + 64 periods), in the
+    bench's launch form; sampled systems replayed one by one by the oracle."""
+    w = W.duffing_rkck()
+    g = run_gpu(w, persistent=1)
+    assert np.all(np.isin(g["status"], [1]))
+    idx = W.sample_indices(w["N"], 40, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    ws = W.subset(w, idx)
+    mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
+    gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    assert mask.sum() >= 10
+    _compare_records(gs, o, mask, 7, 2, tol=1e-8, exact_rows=(6, 9))
+    # every system integrated every period
+    assert np.all(g["nacc"] > 1088 * 50)
+
+
+# ---------------------------------------------------------------------------
+# Keller-Miksis (Sec. 2.2, single frequency), grid corners and interior.
+# ---------------------------------------------------------------------------
+def test_keller_miksis_parity():
+    w = W.keller_miksis(6, 6, 4, 4)
+    A, n = 4, 2
+    mask, o = _nonchaotic(w, 4, 4, cont_rows=(4, 5), rtol=1e-10)
+    g = run_gpu(w)
+    assert np.all(g["status"] == 1)
+    assert mask.sum() >= 18
+    _compare_records(g, o, mask, A, n, tol=1e-8, exact_rows=(6,))
+    # the unforced column (pA = 0) stays at the equilibrium radius
+    pa0 = w["PA"] == 0
+    assert np.all(np.abs(g["records"][:, 4, pa0] - 1.0) < 1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Pressure relief valve with two events, impact action and equilibrium stop
+# (Sec. 7.3), per-sweep and persistent launches.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_valve_parity(persistent):
+    w = W.valve(N=96, n_transient=30, n_record=10)
+    A, n = 5, 3
+    o = run_oracle(w, NTHREADS)
+    o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
+    g = run_gpu(w, persistent=persistent)
+    # stop reasons and impact counts: exact where the two oracle runs agree
+    stable = np.all(o["records"][:, 4] == o2["records"][:, 4], axis=0) & (o["status"] == o2["status"])
+    stable &= np.all(_rel_close(o["records"][:, 5], o2["records"][:, 5], 1e-7, 1e-7), axis=0)
+    assert stable.sum() > 48
+    np.testing.assert_array_equal(g["status"][stable], o["status"][stable])
+    np.testing.assert_array_equal(g["records"][:, 4, stable], o["records"][:, 4, stable])
+    tol = 100 * 1e-9
+    for row in (0, 5, 6, 7, 8):  # max (Poincare section), end state, end time
+        np.testing.assert_array_less(
+            np.abs(g["records"][:, row, stable] - o["records"][:, row, stable]),
+            tol * (1 + np.abs(o["records"][:, row, stable])), err_msg="row %d" % row)
+    # equilibrium for high flow rates (Sec. 7.3)
+    hi = w["p"][3] > 9.0
+    assert np.all(g["status"][hi] == G.ODE_ST_EQUILIBRIUM)
+
+
+# ---------------------------------------------------------------------------
+# Bouncing ball: impact law against its closed form on the GPU too.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", [W.RK4, W.RKCK45])
+def test_bounce_closed_form_on_gpu(scheme):
+    N = 8
+    g0, r0, h0 = 1.0, 0.8, 1.0
+    w = W._base(name="ball", model=W.BOUNCE, scheme=scheme, N=N, h0=0.01, hmax=0.05,
+                td=np.vstack([np.zeros(N), np.full(N, 12.0)]), y0=np.vstack([np.full(N, h0), np.zeros(N)]),
+                p=np.vstack([np.full(N, g0), np.full(N, r0)]), events_on=True, evt_dir=(-1,),
+                evt_tol=(1e-12,), evt_stop=(0,), n_transient=0, n_record=1)
+    g = run_gpu(w)
+    t, v, times = math.sqrt(2 * h0 / g0), math.sqrt(2 * g0 * h0), []
+    while t < 12.0:
+        times.append((t, -v))
+        t += 2 * r0 * v / g0
+        v *= r0
+    np.testing.assert_array_equal(g["ecnt"][0], len(times))
+    np.testing.assert_allclose(g["acc"][4], times[-1][0], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(g["acc"][5], times[-1][1], rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Binary32 right-hand side: the error against the binary64 oracle is measured
+# and reported (no tolerance is claimed); the run must complete.
+# ---------------------------------------------------------------------------
+def test_fp32_rhs_duffing_and_valve_report(tmp_path):
+    rows = []
+    for w in (W.duffing_rkck(16, 8, 10, 4), W.valve(N=64, n_transient=10, n_record=4)):
+        o = run_oracle(w, NTHREADS)
+        g = run_gpu(w, prec=G.ODE_FP32_RHS)
+        A, n = DIMS[w["model"]][2], DIMS[w["model"]][0]
+        assert np.all(np.isfinite(g["records"]))
+        assert np.all(g["status"] > 0)
+        err = np.max(np.abs(g["records"][:, A:A + n] - o["records"][:, A:A + n]))
+        rows.append((w["name"], float(err), float(g["nacc"].sum() / o["nacc"].sum())))
+    for r in rows:
+        print("FP32_RHS %s: max |end state - oracle| = %.3e, accepted steps vs oracle = %.3f" % r)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases: partial warps / blocks, a single system, empty and ragged time
+# domains, NaN parameters, step budget.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 31, 33, 1025])
+def test_ragged_sizes(N):
+    w = W.duffing_rkck(N, 1, 2, 2)
+    g = run_gpu(w)
+    o = run_oracle(w, NTHREADS)
+    assert np.all(g["status"] == 1)
+    assert np.all(_rel_close(g["records"][:, 7:9], o["records"][:, 7:9], 1e-8, 1e-8))
+
+
+def test_empty_and_mixed_time_domains():
+    w = W.duffing_rkck(8, 1, 0, 2)
+    td = w["td"].copy()
+    td[1, 0] = 0.0          # empty domain: nothing to integrate
+    td[1, 1] = -1.0         # reversed: treated as empty
+    td[1, 2] = 1e-3         # shorter than h0
+    td[:, 3] = [5.0, 7.5]   # shifted
+    w = dict(w, td=td)
+    g = run_gpu(w)
+    o = run_oracle(w, NTHREADS)
+    np.testing.assert_array_equal(g["status"], o["status"])
+    np.testing.assert_array_equal(g["nacc"][:2], 0)
+    assert np.all(_rel_close(g["y"], o["y"], 1e-8, 1e-8))
+    np.testing.assert_array_equal(g["records"][:, 9], o["records"][:, 9])
+
+
+def test_nan_parameter_stops_at_hmin_and_budget():
+    w = W.duffing_rkck(4, 1, 0, 1)
+    p = w["p"].copy()
+    p[0, 1] = float("nan")
+    w = dict(w, p=p, hmin=1e-6)
+    g = run_gpu(w)
+    o = run_oracle(w, NTHREADS)
+    np.testing.assert_array_equal(g["status"], o["status"])
+    assert g["status"][1] == G.ODE_ST_HMIN_NAN
+    np.testing.assert_array_equal(g["nrej"], o["nrej"])
+    np.testing.assert_array_equal(g["y"][:, 1], w["y0"][:, 1])
+    # step budget
+    s = gpu_solver(dict(w, p=w["p"]))
+    try:
+        gpu_load(s, w)
+        G.ode_set_step_budget(s, 7)
+        G.ode_solve(s, w["h0"])
+        G.ode_synchronize(s)
+        r = gpu_results(s, w)
+        assert np.all(r["status"] == G.ODE_ST_STEP_BUDGET)
+        assert np.all(r["nacc"] + r["nrej"] == 7)
+    finally:
+        G.ode_destroy(s)
+
+
+# ---------------------------------------------------------------------------
+# Object filling / read-back (Sec. 6.3, 6.10) and device pointers.
+# ---------------------------------------------------------------------------
+def test_linear_and_random_set_get_host_and_device():
+    import torch
+    w = W.duffing_rkck(16, 1, 0, 1)
+    N = w["N"]
+    s = gpu_solver(w)
+    try:
+        pool = 40
+        td = np.arange(2 * pool, dtype=np.float64).reshape(2, pool)
+        y = np.arange(2 * pool, dtype=np.float64).reshape(2, pool) + 1000
+        p = np.arange(2 * pool, dtype=np.float64).reshape(2, pool) + 2000
+        acc = np.arange(7 * pool, dtype=np.float64).reshape(7, pool) + 3000
+        G.ode_linear_set(s, 2, 5, pool, 10, td=td, y=y, p=p, acc=acc)
+        out = [np.zeros((c, N)) for c in (2, 2, 2, 7)]
+        G.ode_linear_get(s, 0, 0, N, N, *out)
+        for got, src in zip(out, (td, y, p, acc)):
+            np.testing.assert_array_equal(got[:, 2:12], src[:, 5:15])
+        io = np.array([15, 0, 7], dtype=np.int32)
+        ip = np.array([1, 39, 20], dtype=np.int32)
+        G.ode_random_set(s, io, ip, pool, 3, p=p, copy_mode=G.ODE_PARAM)
+        pp = np.zeros((2, N))
+        G.ode_linear_get(s, 0, 0, N, N, p=pp, copy_mode=G.ODE_PARAM)
+        np.testing.assert_array_equal(pp[:, io], p[:, ip])
+        # device pointers (torch tensors)
+        dp = torch.tensor(p, device="cuda")
+        dio, dip = torch.tensor(io, device="cuda"), torch.tensor(ip, device="cuda")
+        G.ode_random_set(s, dio, dip, pool, 3, p=dp * 2, copy_mode=G.ODE_PARAM)
+        torch.cuda.synchronize()
+        back = torch.zeros((2, pool), dtype=torch.float64, device="cuda")
+        G.ode_random_get(s, dio, dip, pool, 3, p=back, copy_mode=G.ODE_PARAM)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(back.cpu().numpy()[:, ip], 2 * p[:, ip])
+        # invalid ranges are rejected with a message
+        with pytest.raises(G.ODEError) as e:
+            G.ode_linear_set(s, N - 1, 0, pool, 2, td=td, copy_mode=G.ODE_TIMEDOMAIN)
+        assert "range" in str(e.value)
+    finally:
+        G.ode_destroy(s)
+
+
+def test_device_records_and_single_solve_match_run_periods():
+    import torch
+    w = W.duffing_rkck(8, 2, 0, 3)
+    N, A, n = w["N"], 7, 2
+    ref = run_gpu(w)
+    s = gpu_solver(w)
+    try:
+        gpu_load(s, w)
+        rec = torch.zeros((3, A + n + 1, N), dtype=torch.float64, device="cuda")
+        G.ode_run_periods(s, w["h0"], 0, 3, rec, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(rec.cpu().numpy(), ref["records"])
+        # three single Solve calls give the same end state
+        gpu_load(s, w)
+        for _ in range(3):
+            G.ode_solve(s, w["h0"])
+        G.ode_synchronize(s)
+        r = gpu_results(s, w)
+        np.testing.assert_array_equal(r["y"], ref["y"])
+    finally:
+        G.ode_destroy(s)
+
+
+def test_invalid_arguments_are_reported():
+    with pytest.raises(G.ODEError):
+        G.ode_create(7, 0, 0, 10, 0)
+    with pytest.raises(G.ODEError) as e:
+        G.ode_create(G.ODE_KELLER_MIKSIS, G.ODE_RKCK45, G.ODE_FP32_RHS, 10, 0)
+    assert "binary64" in str(e.value)
+    s = G.ode_create(G.ODE_DUFFING, G.ODE_RKCK45, G.ODE_FP64, 4, 0)
+    try:
+        with pytest.raises(G.ODEError):
+            G.ode_set_tolerances(s, [1e-9, 1e-9], [1e-9, 1e-9], 1.0, 2.0, 5.0, 0.1)
+        with pytest.raises(G.ODEError):
+            G.ode_set_launch(s, 48, 0)
+        with pytest.raises(G.ODEError):
+            G.ode_solve(s, -1.0)
+        with pytest.raises(G.ODEError):
+            G.ode_set_events(s, 1, [2], [1e-6], [0], 0)
+    finally:
+        G.ode_destroy(s)
+
+
+def test_watchdog_stops_a_launch_that_runs_too_long():
+    """Failure detection without a fault: a launch whose threads exceed the
+    time limit stop their systems (status TIMEOUT) and the next synchronizing
+    call reports ODE_ERR_TIMEOUT; the context stays usable."""
+    w = W.duffing_rkck(64, 4, 0, 400)
+    for persistent in (0, 1):
+        s = gpu_solver(w, persistent=persistent)
+        try:
+            gpu_load(s, w)
+            G.ode_set_time_limit(s, 1e-3)
+            G.ode_run_periods(s, w["h0"], 0, 400, None)
+            with pytest.raises(G.ODEError) as e:
+                G.ode_synchronize(s)
+            assert e.value.code == G.ODE_ERR_TIMEOUT
+            status = np.zeros(w["N"], dtype=np.int32)
+            G.ode_get_status(s, status)
+            assert np.any(status == G.ODE_ST_TIMEOUT)
+            # the solver and the context still work
+            G.ode_set_time_limit(s, 300.0)
+            gpu_load(s, w)
+            G.ode_run_periods(s, w["h0"], 0, 1, None)
+            G.ode_synchronize(s)
+            G.ode_get_status(s, status)
+            assert np.all(status == G.ODE_ST_TEND)
+        finally:
+            G.ode_destroy(s)
+
+
+def test_kernels_do_not_spill():
+    for model in (0, 1, 2, 3):
+        for scheme in (0, 1):
+            for prec in ((0, 1) if model != 1 else (0,)):
+                for pers in (0, 1):
+                    info = G.ode_kernel_info(model, scheme, prec, pers)
+                    assert info["blocks_per_sm"] >= 1
+                    assert info["regs"] <= 255
