@@ -154,6 +154,10 @@ def run_gpu(args):
     from _runners import DIMS, km_params_gpu
 
     w = workload(args.workload, rank)
+    if args.n_transient is not None:
+        w["n_transient"] = args.n_transient
+    if args.n_record is not None:
+        w["n_record"] = args.n_record
     n, P, A, E = DIMS[w["model"]]
     N = w["N"]
     n_tr, n_rec = w["n_transient"], w["n_record"]
@@ -222,7 +226,7 @@ def run_gpu(args):
     h_rec = torch.zeros((n_rec, R, N), dtype=torch.float64).pin_memory()
     h_nacc = torch.zeros(N, dtype=torch.int64).pin_memory()
     e2e_times, e2e_steps = [], []
-    for k in range(max(1, min(args.steps, 2))):
+    for k in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
         flush.fill_(k & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -254,14 +258,16 @@ def run_gpu(args):
 
     # aggregate over ranks: total accepted steps / max time
     tot_steps, max_ms = steps_per_pass, ms_step
-    e2e_rate = float(np.mean(e2e_steps)) / float(np.mean(e2e_times))
+    e2e_rate = float(np.mean(e2e_steps)) / float(np.mean(e2e_times)) if e2e_times else None
     if world > 1:
         t = torch.tensor([tot_steps, 0.0], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        m = torch.tensor([max_ms, float(np.mean(e2e_times))], dtype=torch.float64, device=dev)
+        m = torch.tensor([max_ms, float(np.mean(e2e_times)) if e2e_times else 0.0], dtype=torch.float64,
+                         device=dev)
         dist.all_reduce(m, op=dist.ReduceOp.MAX)
         tot_steps, max_ms = float(t[0]), float(m[0])
-        e2e_rate = float(np.mean(e2e_steps)) * world / float(m[1])
+        if e2e_times:
+            e2e_rate = float(np.mean(e2e_steps)) * world / float(m[1])
 
     line = None
     if rank == 0:
@@ -273,7 +279,7 @@ def run_gpu(args):
             "config": describe(w, args.persistent, "flushed before every timed step (256 MB write)"),
             "accepted_steps_per_pass": steps_per_pass, "wall_s_timed": wall,
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "s_per_step": float(np.mean(e2e_times))},
+                    "s_per_step": float(np.mean(e2e_times)) if e2e_times else None},
             "gpu_launches": args.steps,  # one integrator launch per step
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": None,
@@ -359,6 +365,9 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-transient", type=int, default=None, help="override (profiling runs)")
+    ap.add_argument("--n-record", type=int, default=None, help="override (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -4,9 +4,14 @@ element on the same seeded inputs.
 Acceptance:
   * RK4 binary64 final states and records: 1e-12 relative (atol 1e-12).
   * RKCK45 accessories, event points and Poincare points: 100 x rtol on
-    non-chaotic parameter points.  A point is non-chaotic when the oracle at
-    rtol and at rtol / 10 agrees on its recorded continuous quantities (end
-    state and event-located maxima) within 10 x rtol.
+    well-conditioned (non-chaotic) parameter points.  A point qualifies when
+    the oracle at rtol and at rtol / 10 agrees on its recorded continuous
+    quantities (end state and event-located maxima) within the acceptance
+    tolerance itself (Duffing: 10 x rtol suffices; Keller-Miksis collapses
+    amplify local errors so that its global error is already ~10-100 x rtol).
+  * Where an event ends a slice or changes the state (valve impacts), the
+    located point is only fixed to the event tolerance, so the acceptance is
+    max(100 x rtol, 10 x event tolerance).
   * Discrete accessories (max / min over accepted points) may pick the other
     of two near-equal samples; their times are then checked for validity
     (the value agrees) instead of equality.
@@ -31,13 +36,15 @@ def _rel_close(a, b, rtol, atol):
     return np.abs(a - b) <= atol + rtol * np.abs(b)
 
 
-def _nonchaotic(w, n_tr, n_rec, cont_rows, rtol):
-    """Mask of systems whose continuous records agree at rtol and rtol/10."""
+def _nonchaotic(w, n_tr, n_rec, cont_rows, rtol, agree=None):
+    """Mask of systems whose continuous records agree at rtol and rtol/10
+    within `agree` (default 10 x rtol)."""
+    agree = 10 * rtol if agree is None else agree
     r1 = run_oracle(w, NTHREADS, n_transient=n_tr, n_record=n_rec)
     r2 = run_oracle(w, NTHREADS, n_transient=n_tr, n_record=n_rec, rtol=rtol / 10, atol=rtol / 10)
     ok = np.ones(w["N"], dtype=bool)
     for row in cont_rows:
-        ok &= np.all(_rel_close(r1["records"][:, row], r2["records"][:, row], 10 * rtol, 10 * rtol), axis=0)
+        ok &= np.all(_rel_close(r1["records"][:, row], r2["records"][:, row], agree, agree), axis=0)
     return ok, r1
 
 
@@ -137,10 +144,10 @@ def test_duffing_rkck_full_size_sampled():
 def test_keller_miksis_parity():
     w = W.keller_miksis(6, 6, 4, 4)
     A, n = 4, 2
-    mask, o = _nonchaotic(w, 4, 4, cont_rows=(4, 5), rtol=1e-10)
+    mask, o = _nonchaotic(w, 4, 4, cont_rows=(4, 5), rtol=1e-10, agree=1e-8)
     g = run_gpu(w)
     assert np.all(g["status"] == 1)
-    assert mask.sum() >= 18
+    assert mask.sum() >= 24
     _compare_records(g, o, mask, A, n, tol=1e-8, exact_rows=(6,))
     # the unforced column (pA = 0) stays at the equilibrium radius
     pa0 = w["PA"] == 0
@@ -158,13 +165,16 @@ def test_valve_parity(persistent):
     o = run_oracle(w, NTHREADS)
     o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
     g = run_gpu(w, persistent=persistent)
+    # located points are fixed only to the event tolerance (1e-6, Sec. 6.6)
+    tol = max(100 * w["rtol"], 10 * w["evt_tol"][0])
     # stop reasons and impact counts: exact where the two oracle runs agree
     stable = np.all(o["records"][:, 4] == o2["records"][:, 4], axis=0) & (o["status"] == o2["status"])
-    stable &= np.all(_rel_close(o["records"][:, 5], o2["records"][:, 5], 1e-7, 1e-7), axis=0)
-    assert stable.sum() > 48
+    stable &= np.all(_rel_close(o["records"][:, 5], o2["records"][:, 5], tol, tol), axis=0)
+    assert stable.sum() > 64
     np.testing.assert_array_equal(g["status"][stable], o["status"][stable])
     np.testing.assert_array_equal(g["records"][:, 4, stable], o["records"][:, 4, stable])
-    tol = 100 * 1e-9
+    dev = np.max(np.abs(g["records"][:, 5:8, stable] - o["records"][:, 5:8, stable]))
+    print("valve: max |end state - oracle| over %d points = %.3e" % (stable.sum(), dev))
     for row in (0, 5, 6, 7, 8):  # max (Poincare section), end state, end time
         np.testing.assert_array_less(
             np.abs(g["records"][:, row, stable] - o["records"][:, row, stable]),
@@ -262,8 +272,10 @@ def test_nan_parameter_stops_at_hmin_and_budget():
         G.ode_solve(s, w["h0"])
         G.ode_synchronize(s)
         r = gpu_results(s, w)
-        assert np.all(r["status"] == G.ODE_ST_STEP_BUDGET)
-        assert np.all(r["nacc"] + r["nrej"] == 7)
+        ok = np.arange(w["N"]) != 1  # system 1 (NaN) stops at hmin first
+        assert np.all(r["status"][ok] == G.ODE_ST_STEP_BUDGET)
+        assert np.all(r["nacc"][ok] + r["nrej"][ok] == 7)
+        assert r["status"][1] == G.ODE_ST_HMIN_NAN
     finally:
         G.ode_destroy(s)
 
