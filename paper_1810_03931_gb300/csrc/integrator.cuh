@@ -47,19 +47,62 @@ struct StageType { using type = double; };
 template <>
 struct StageType<kFP32RHS> { using type = float; };
 
+// ---- harmonic forcing ------------------------------------------------------
+// cos d and sin d for |d| <= 0.1 from their Taylor series to degree 8 and 9
+// (the first omitted terms are below 3e-17 relative on that interval).
+__device__ __forceinline__ void small_angle(double d, double& cd, double& sd) {
+  const double u = d * d;
+  cd = fma(fma(fma(fma(u, 1.0 / 40320.0, -1.0 / 720.0), u, 1.0 / 24.0), u, -0.5), u, 1.0);
+  sd = d * fma(fma(fma(fma(u, 1.0 / 362880.0, -1.0 / 5040.0), u, 1.0 / 120.0), u, -1.0 / 6.0), u, 1.0);
+}
+
+constexpr double kSmallAngle = 0.1;
+
 // ---- one trial step --------------------------------------------------------
 // From (t, y) with step hs and the cached first stage k1 = f(t, y), compute
 // the new state ynew and (RKCK45) the error estimate err = hs * sum e_i k_i.
 // Stage states and f are in precision T; ynew and err are binary64.
+// Harmonic forcing in binary64: (C, S) = (cos, sin)(omega t) at the lane's t;
+// a stage at t + c hs gets (cos, sin)(omega (t + c hs)) by angle addition with
+// d = omega c hs, and the c = 1 stage returns them in (Cn, Sn) as the anchor
+// of the next step.  Large d (long steps) falls back to sincos.
 template <class M, int SCHEME, int PREC>
 struct Stepper {
   static constexpr int n = M::N, P = M::P;
   using T = typename StageType<PREC>::type;
+  static constexpr bool kRotate = (PREC == kFP64) && (M::kForcing != kNoForcing);
+
+  static __device__ __forceinline__ Stage<T> stage_at(double t, double hs, T tb, T h, double c,
+                                                      const T (&mct)[3], double C, double S,
+                                                      double w) {
+    Stage<T> st;
+    if constexpr (kRotate) {
+      st.t = t + c * hs;
+      const double d = w * (c * hs);
+      if (fabs(d) <= kSmallAngle) {
+        double cd, sd;
+        small_angle(d, cd, sd);
+        st.c = C * cd - S * sd;
+        st.s = S * cd + C * sd;
+      } else {
+        sincos(w * st.t, &st.s, &st.c);
+      }
+    } else {
+      st.t = tb + (T)c * h;
+      if constexpr (M::kForcing != kNoForcing) {
+        sincos_t(M::omega(mct) * st.t, &st.s, &st.c);
+      } else {
+        st.c = st.s = (T)0;
+      }
+    }
+    return st;
+  }
 
   static __device__ __forceinline__ void step(double t, const double (&y)[n], double hs,
                                               const T (&pt)[P], const T (&mct)[3],
-                                              const T (&k1)[n], double (&ynew)[n],
-                                              double (&err)[n]) {
+                                              const T (&k1)[n], double C, double S, double w,
+                                              double (&ynew)[n], double (&err)[n], double& Cn,
+                                              double& Sn) {
     T yb[n];
 #pragma unroll
     for (int m = 0; m < n; m++) yb[m] = (T)y[m];
@@ -71,25 +114,28 @@ struct Stepper {
       T k2[n], k3[n], k4[n], k5[n], k6[n];
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a21 * k1[m]);
-      M::template rhs<T>(tb + (T)c2 * h, ys, pt, mct, k2);
+      M::template rhs<T>(stage_at(t, hs, tb, h, c2, mct, C, S, w), ys, pt, mct, k2);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a31 * k1[m] + (T)a32 * k2[m]);
-      M::template rhs<T>(tb + (T)c3 * h, ys, pt, mct, k3);
+      M::template rhs<T>(stage_at(t, hs, tb, h, c3, mct, C, S, w), ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h, (T)a41 * k1[m] + (T)a42 * k2[m] + (T)a43 * k3[m]);
-      M::template rhs<T>(tb + (T)c4 * h, ys, pt, mct, k4);
+      M::template rhs<T>(stage_at(t, hs, tb, h, c4, mct, C, S, w), ys, pt, mct, k4);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a51 * k1[m] + (T)a52 * k2[m] + (T)a53 * k3[m] + (T)a54 * k4[m]);
-      M::template rhs<T>(tb + (T)c5 * h, ys, pt, mct, k5);
+      const Stage<T> s5 = stage_at(t, hs, tb, h, c5, mct, C, S, w);
+      M::template rhs<T>(s5, ys, pt, mct, k5);
+      Cn = (double)s5.c;
+      Sn = (double)s5.s;
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a61 * k1[m] + (T)a62 * k2[m] + (T)a63 * k3[m] + (T)a64 * k4[m] +
                           (T)a65 * k5[m]);
-      M::template rhs<T>(tb + (T)c6 * h, ys, pt, mct, k6);
+      M::template rhs<T>(stage_at(t, hs, tb, h, c6, mct, C, S, w), ys, pt, mct, k6);
 #pragma unroll
       for (int m = 0; m < n; m++) {
         // binary64 state update and error estimate
@@ -102,15 +148,19 @@ struct Stepper {
     } else {
       T k2[n], k3[n], k4[n];
       const T half = (T)0.5;
+      const Stage<T> sh = stage_at(t, hs, tb, h, 0.5, mct, C, S, w);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
-      M::template rhs<T>(tb + half * h, ys, pt, mct, k2);
+      M::template rhs<T>(sh, ys, pt, mct, k2);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k2[m]);
-      M::template rhs<T>(tb + half * h, ys, pt, mct, k3);
+      M::template rhs<T>(sh, ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
-      M::template rhs<T>(tb + h, ys, pt, mct, k4);
+      const Stage<T> s4 = stage_at(t, hs, tb, h, 1.0, mct, C, S, w);
+      M::template rhs<T>(s4, ys, pt, mct, k4);
+      Cn = (double)s4.c;
+      Sn = (double)s4.s;
 #pragma unroll
       for (int m = 0; m < n; m++) {
         const T sb = (T)(1.0 / 6.0) * k1[m] + (T)(1.0 / 3.0) * k2[m] + (T)(1.0 / 3.0) * k3[m] +
@@ -133,19 +183,17 @@ struct Stepper {
   }
 };
 
-// x^(-1/5) for x in [1e-6, 1e6]: a binary32 seed refined by two Newton steps
-// for z^-5 = x in binary64, z <- z + z (1 - x z^5) / 5 (each step squares the
-// relative error: ~1e-7 -> ~1e-14 -> rounding).  About a dozen binary64
+// x^(-1/5) for x within the clamping range of the step-size factor: a
+// binary32 seed (relative error ~2e-7) refined by one Newton step for
+// z^-5 = x in binary64, z <- z + z (1 - x z^5) / 5, which squares the error
+// to ~2e-13 -- far below the rounding noise of the error estimate itself
+// (the estimate is a difference of nearly equal sums).  Six binary64
 // operations instead of a general pow().
 __device__ __forceinline__ double rpow_fifth(double x) {
-  double z = (double)exp2f(-0.2f * __log2f((float)x));
-#pragma unroll
-  for (int it = 0; it < 2; it++) {
-    const double z2 = z * z;
-    const double r = fma(-x, z2 * z2 * z, 1.0);
-    z = fma(0.2 * z, r, z);
-  }
-  return z;
+  const double z = (double)exp2f(-0.2f * __log2f((float)x));
+  const double z2 = z * z;
+  const double r = fma(-x, z2 * z2 * z, 1.0);
+  return fma(0.2 * z, r, z);
 }
 
 // Is event j crossed in its allowed direction between F_old (outside the
@@ -188,6 +236,9 @@ struct Lane {
   int ecnt[E];
   T k1[n];
   double lo, hi, yhi[n];
+  double fC, fS;    // cos, sin of omega t at the lane's t (binary64 forcing)
+  double fCn, fSn;  // the same at t + hs of the last normal trial step
+  double w;         // forcing angular frequency
 
   __device__ __forceinline__ void load(const KArgs& a) {
     const int N = a.N;
@@ -220,6 +271,10 @@ struct Lane {
     a.nrej[sys] += nrej;
   }
 
+  __device__ __forceinline__ void anchor_forcing() {
+    if constexpr (St::kRotate) sincos(w * t, &fS, &fC);
+  }
+
   // Start a slice: Initialization hook (Sec. 6.8), event state at t0 (a
   // point already inside a zone is in the leaving state and is not detected,
   // Sec. 4 / Sec. 7.2), initial step (Sec. 6.4).
@@ -250,6 +305,7 @@ struct Lane {
     steps = 0;
     k1ok = false;
     locating = false;
+    anchor_forcing();
   }
 
   // End of a slice: Finalization time-domain update (Sec. 6.8) and record.
@@ -282,6 +338,14 @@ struct Lane {
   __device__ __forceinline__ void accept(const Props& pr, double tnew, const double (&ynew)[n],
                                          bool last, bool located) {
     t = tnew;
+    if constexpr (St::kRotate) {
+      if (located) {
+        anchor_forcing();
+      } else {
+        fC = fCn;
+        fS = fSn;
+      }
+    }
 #pragma unroll
     for (int m = 0; m < n; m++) y[m] = ynew[m];
     nacc++;
@@ -364,11 +428,23 @@ struct Lane {
       T yb[n];
 #pragma unroll
       for (int m = 0; m < n; m++) yb[m] = (T)y[m];
-      M::template rhs<T>((T)t, yb, pt, mct, k1);
+      Stage<T> st0;
+      if constexpr (St::kRotate) {
+        st0.t = t;
+        st0.c = fC;
+        st0.s = fS;
+      } else {
+        st0 = St::stage_at(t, 0.0, (T)t, (T)0, 0.0, mct, 0.0, 0.0, 0.0);
+      }
+      M::template rhs<T>(st0, yb, pt, mct, k1);
       k1ok = true;
     }
-    double ynew[n], err[n];
-    St::step(t, y, hs, pt, mct, k1, ynew, err);
+    double ynew[n], err[n], Cn = 0.0, Sn = 0.0;
+    St::step(t, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
+    if (!locating) {
+      fCn = Cn;
+      fSn = Sn;
+    }
 
     if (locating) {
       loc_it++;
@@ -401,15 +477,36 @@ struct Lane {
     steps++;
     if constexpr (SCHEME == kRKCK45) {
       // error ratio and step-size control (Sec. 3, Sec. 6.5)
-      double errr = 0.0;
-      bool finite = true;
+      // max_m |err_m| / sc_m with a single division: every ratio is brought
+      // over the common denominator prod_m sc_m
+      double sc[n], num[n];
+#pragma unroll
+      for (int m = 0; m < n; m++) sc[m] = pr.atol[m] + pr.rtol[m] * fmax(fabs(y[m]), fabs(ynew[m]));
+      double den = 1.0;
 #pragma unroll
       for (int m = 0; m < n; m++) {
-        const double sc = pr.atol[m] + pr.rtol[m] * fmax(fabs(y[m]), fabs(ynew[m]));
-        const double r = fabs(err[m]) / sc;
-        errr = fmax(errr, r);
-        finite = finite && isfinite(r) && isfinite(ynew[m]);
+        num[m] = fabs(err[m]);
+#pragma unroll
+        for (int k = 0; k < n; k++)
+          if (k != m) num[m] *= sc[k];
+        den *= sc[m];
       }
+      double nmax = num[0];
+#pragma unroll
+      for (int m = 1; m < n; m++) nmax = fmax(nmax, num[m]);
+      double errr = nmax / den;
+      if (!(den > 0.0) || !isfinite(den) || !isfinite(nmax)) {
+        // out of range for the common denominator: one division per ratio
+        errr = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; m++) {
+          const double r = fabs(err[m]) / sc[m];
+          errr = (r > errr || isnan(r)) ? r : errr;
+        }
+      }
+      bool finite = isfinite(errr);
+#pragma unroll
+      for (int m = 0; m < n; m++) finite = finite && isfinite(ynew[m]) && !isnan(num[m]);
       const bool at_min = hs <= pr.hmin;
       if (!finite) {
         nrej++;
@@ -494,6 +591,10 @@ __global__ void __launch_bounds__(256) ode_kernel(const KArgs a) {
   L_t L;
 #pragma unroll
   for (int m = 0; m < 3; m++) L.mct[m] = (T)a.pr.mc[m];
+  {
+    double mcd[3] = {a.pr.mc[0], a.pr.mc[1], a.pr.mc[2]};
+    L.w = M::omega(mcd);
+  }
 
   bool active;
   if constexpr (PERSIST) {

@@ -14,10 +14,23 @@
 
 namespace odegpu {
 
-__device__ __forceinline__ float cos_t(float x) { return cosf(x); }
-__device__ __forceinline__ double cos_t(double x) { return cos(x); }
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+
+// Time dependence seen by a right-hand-side evaluation: the stage time t and,
+// for harmonically forced models, c = cos(omega t) and s = sin(omega t) of
+// the model's forcing frequency omega (supplied by the integrator, which
+// advances them by angle addition instead of calling cos per stage).
+template <class T>
+struct Stage {
+  T t;
+  T c;
+  T s;
+};
+
+enum Forcing { kNoForcing = 0, kCosForcing = 1, kSinCosForcing = 2 };
 
 // Ordinary accessories shared by all models (Sec. 6.7): running maximum and
 // minimum of y1 over accepted points, with their times.
@@ -36,12 +49,16 @@ __device__ __forceinline__ void acc_minmax(double t, double y1, double* a) {
 struct Duffing {
   static constexpr int N = 2, P = 2, A = 7, E = 1;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kForcing = kCosForcing;  // cos(omega t), omega = mc[2]
 
   template <class T>
-  static __device__ __forceinline__ void rhs(T t, const T (&y)[N], const T (&p)[P],
+  static __device__ __forceinline__ T omega(const T (&mc)[3]) { return mc[2]; }
+  template <class T>
+  static __device__ __forceinline__ void rhs(const Stage<T>& st, const T (&y)[N], const T (&p)[P],
                                              const T (&mc)[3], T (&f)[N]) {
     f[0] = y[1];
-    f[1] = mc[0] * y[0] - mc[1] * (y[0] * y[0] * y[0]) - p[0] * y[1] + p[1] * cos_t(mc[2] * t);
+    // delta y1 - c3 y1^3 - k y2 + B cos(omega t), as y1 (delta - c3 y1^2) ...
+    f[1] = y[0] * (mc[0] - mc[1] * (y[0] * y[0])) - p[0] * y[1] + p[1] * st.c;
   }
   static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
                                                 double (&F)[E]) {
@@ -72,16 +89,18 @@ struct Duffing {
 struct KellerMiksis {
   static constexpr int N = 2, P = 13, A = 4, E = 1;
   static constexpr bool kHasFP32 = false;
+  static constexpr int kForcing = kSinCosForcing;  // sin, cos of 2 pi tau
 
   template <class T>
-  static __device__ __forceinline__ void rhs(T tau, const T (&y)[N], const T (&C)[P],
+  static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)(2.0 * CUDART_PI); }
+  template <class T>
+  static __device__ __forceinline__ void rhs(const Stage<T>& st, const T (&y)[N], const T (&C)[P],
                                              const T (&)[3], T (&f)[N]) {
     const double y1 = y[0], y2 = y[1];
     const double rx = 1.0 / y1;
-    double s1, c1;
-    sincospi(2.0 * tau, &s1, &c1);  // sin, cos of 2 pi tau
+    const double s1 = st.s, c1 = st.c;  // sin, cos of 2 pi tau
     double s2 = 0.0, c2 = 0.0;
-    if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * tau + C[12], &s2, &c2);
+    if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * st.t + C[12], &s2, &c2);
     const double one_c9y2 = 1.0 + C[9] * y2;
     const double num = (C[0] + C[1] * y2) * pow(rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
                        C[4] * y2 * rx - (1.0 - C[9] * y2 * (1.0 / 3.0)) * 1.5 * y2 * y2 -
@@ -114,10 +133,13 @@ struct KellerMiksis {
 struct Valve {
   static constexpr int N = 3, P = 5, A = 5, E = 2;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kForcing = kNoForcing;
 
   template <class T>
-  static __device__ __forceinline__ void rhs(T, const T (&y)[N], const T (&p)[P], const T (&)[3],
-                                             T (&f)[N]) {
+  static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)0; }
+  template <class T>
+  static __device__ __forceinline__ void rhs(const Stage<T>&, const T (&y)[N], const T (&p)[P],
+                                             const T (&)[3], T (&f)[N]) {
     f[0] = y[1];
     f[1] = -p[0] * y[1] - (y[0] + p[1]) + y[2];
     f[2] = p[2] * (p[3] - y[0] * sqrt_t(y[2]));
@@ -150,10 +172,13 @@ struct Valve {
 struct Bounce {
   static constexpr int N = 2, P = 2, A = 6, E = 1;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kForcing = kNoForcing;
 
   template <class T>
-  static __device__ __forceinline__ void rhs(T, const T (&y)[N], const T (&p)[P], const T (&)[3],
-                                             T (&f)[N]) {
+  static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)0; }
+  template <class T>
+  static __device__ __forceinline__ void rhs(const Stage<T>&, const T (&y)[N], const T (&p)[P],
+                                             const T (&)[3], T (&f)[N]) {
     f[0] = y[1];
     f[1] = -p[0];
   }

@@ -158,30 +158,69 @@ def test_keller_miksis_parity():
 # Pressure relief valve with two events, impact action and equilibrium stop
 # (Sec. 7.3), per-sweep and persistent launches.
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("persistent", [0, 1])
-def test_valve_parity(persistent):
-    w = W.valve(N=96, n_transient=30, n_record=10)
-    A, n = 5, 3
-    o = run_oracle(w, NTHREADS)
-    o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
-    g = run_gpu(w, persistent=persistent)
-    # located points are fixed only to the event tolerance (1e-6, Sec. 6.6)
-    tol = max(100 * w["rtol"], 10 * w["evt_tol"][0])
-    # stop reasons and impact counts: exact where the two oracle runs agree
+def _valve_stable(w, o, o2, tol):
+    """Systems whose stop reasons, impact counts and end states agree
+    between the oracle at rtol and at rtol / 10."""
     stable = np.all(o["records"][:, 4] == o2["records"][:, 4], axis=0) & (o["status"] == o2["status"])
-    stable &= np.all(_rel_close(o["records"][:, 5], o2["records"][:, 5], tol, tol), axis=0)
-    assert stable.sum() > 64
+    stable &= np.all(_rel_close(o["records"][:, 5:8], o2["records"][:, 5:8], tol, tol), axis=(0, 1))
+    return stable
+
+
+def _valve_compare(g, o, stable, tol):
     np.testing.assert_array_equal(g["status"][stable], o["status"][stable])
     np.testing.assert_array_equal(g["records"][:, 4, stable], o["records"][:, 4, stable])
-    dev = np.max(np.abs(g["records"][:, 5:8, stable] - o["records"][:, 5:8, stable]))
-    print("valve: max |end state - oracle| over %d points = %.3e" % (stable.sum(), dev))
     for row in (0, 5, 6, 7, 8):  # max (Poincare section), end state, end time
         np.testing.assert_array_less(
             np.abs(g["records"][:, row, stable] - o["records"][:, row, stable]),
             tol * (1 + np.abs(o["records"][:, row, stable])), err_msg="row %d" % row)
-    # equilibrium for high flow rates (Sec. 7.3)
-    hi = w["p"][3] > 9.0
-    assert np.all(g["status"][hi] == G.ODE_ST_EQUILIBRIUM)
+    dev = np.max(np.abs(g["records"][:, 5:8, stable] - o["records"][:, 5:8, stable]))
+    print("valve: max |end state - oracle| over %d points = %.3e" % (stable.sum(), dev))
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_valve_parity(persistent):
+    """Two events (maximum with stop 1, impact with action), located to 1e-10
+    so that the location error is below the 100 x rtol acceptance."""
+    w = W.valve(N=96, n_transient=30, n_record=10)
+    w = dict(w, evt_tol=(1e-10, 1e-10))
+    o = run_oracle(w, NTHREADS)
+    o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
+    tol = 100 * w["rtol"]
+    stable = _valve_stable(w, o, o2, tol)
+    assert stable.sum() >= 80
+    g = run_gpu(w, persistent=persistent)
+    _valve_compare(g, o, stable, tol)
+
+
+def test_valve_parity_paper_event_tolerance():
+    """The paper's event tolerance 1e-6 (Sec. 6.6): a located point is fixed
+    only to |F| <= 1e-6, so the acceptance is 100 x that tolerance."""
+    w = W.valve(N=96, n_transient=30, n_record=10)
+    o = run_oracle(w, NTHREADS)
+    o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
+    tol = 100 * w["evt_tol"][0]
+    stable = _valve_stable(w, o, o2, tol)
+    assert stable.sum() >= 75
+    g = run_gpu(w, persistent=1)
+    _valve_compare(g, o, stable, tol)
+
+
+def test_valve_equilibrium_stop_high_flow_rate():
+    """q > 8.5 settles to the equilibrium inside the event-0 zone and stops
+    after MaximumIterationForEquilibrium = 50 steps (Sec. 4, Sec. 7.3)."""
+    w = W.valve(N=16, n_transient=240, n_record=10)
+    p = w["p"].copy()
+    p[3] = np.linspace(9.0, 10.0, 16)
+    w = dict(w, p=p)
+    g = run_gpu(w, persistent=1)
+    o = run_oracle(w, NTHREADS)
+    assert np.all(o["status"] == G.ODE_ST_EQUILIBRIUM)
+    np.testing.assert_array_equal(g["status"], o["status"])
+    # each recorded iteration ends 50 steps after entering the zone
+    np.testing.assert_allclose(g["records"][:, 5:8], o["records"][:, 5:8], rtol=1e-7, atol=1e-7)
+    q, d = p[3], w["p"][1][0]
+    y1 = g["y"][0]
+    np.testing.assert_allclose(y1 * np.sqrt(y1 + d), q, rtol=1e-4)
 
 
 # ---------------------------------------------------------------------------
