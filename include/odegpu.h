@@ -248,6 +248,65 @@ int ode_kernel_info(int model, int scheme, int prec, int persistent, int block_s
  * the roofline peak of the arithmetic-bound integrators. */
 int ode_probe_fma_peak(int device, double *dfma_per_s, double *ffma_per_s);
 
+/* ---- integration without allocation ---------------------------------------- */
+
+/* Settings of ode_run_periods_noalloc (host memory, read during the call).
+ * rtol / atol: first n entries used; direction / tolerance / stop_count:
+ * first E entries used (E, n of the model, see enum ode_model); the meaning
+ * and limits of every field are those of ode_set_tolerances, ode_set_events,
+ * ode_set_model_constants (unused entries 0), ode_set_time_domain_mode,
+ * ode_set_step_budget and ode_set_time_limit. */
+typedef struct ode_noalloc_settings {
+    int model, scheme, prec;
+    double rtol[4], atol[4];
+    double h_max, h_min, grow_limit, shrink_limit;
+    int events_enabled;
+    int direction[2];
+    double tolerance[2];
+    int stop_count[2];
+    int max_steps_in_zone;
+    int time_domain_mode;
+    long long max_steps_per_slice;
+    double time_limit_s;
+    double model_constants[8];
+} ode_noalloc_settings;
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory themselves or through the library: code whose
+ * device memory is owned by another allocator's pool (a framework caching
+ * allocator, where a raw cudaMalloc beside the pool fragments memory and may
+ * fail unpredictably), and latency-bound loops that cannot afford the implicit
+ * device synchronisation of cudaMalloc / cudaFree.
+ *
+ * It does what ode_run_periods does on a persistent launch -- n_transient +
+ * n_record consecutive slices of every system in one kernel, records written
+ * after each of the last n_record slices -- without a solver object and
+ * without allocating: td [2][N], y [n][N], p [P][N], acc [A][N] (read and
+ * updated in place) and records [n_record][A+n+1][N] (may be NULL) are the
+ * caller's DEVICE arrays on `device`, laid out as in ode_run_periods.  The
+ * kernel's other global memory (work-queue head, watchdog flag, per-system
+ * stop status, event counters and step counters) is a fixed array inside the
+ * library, reserved on every GPU that loads the library's device code and
+ * kept until the process exits; it holds at most 65536 systems, and larger
+ * n_systems are rejected with ODE_ERR_INVALID_ARG.  status [N] (int) and
+ * accepted [N] (long long), device arrays or NULL, receive the stop status
+ * and the accepted-step count of this call.
+ *
+ * The call only enqueues work on `stream` and calls no cudaMalloc, cudaFree
+ * or other allocating routine.  Its first call on a device looks up the
+ * array's device address (once per device); make that first call before any
+ * stream capture.  Every call reuses the same array, which keeps the last
+ * call's contents; the call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array
+ * and must be serialised by the caller.  A watchdog stop shows as
+ * ODE_ST_TIMEOUT in `status`.  Returns ODE_OK or an ODE_ERR_* code; *message
+ * (if message is not NULL) points to a thread-local description of the last
+ * failure of this call. */
+int ode_run_periods_noalloc(const ode_noalloc_settings *settings, int n_systems, int device,
+                            double h0, int n_transient, int n_record, double *td, double *y,
+                            const double *p, double *acc, double *records, int *status,
+                            long long *accepted, void *stream, const char **message);
+
 #ifdef __cplusplus
 }
 #endif

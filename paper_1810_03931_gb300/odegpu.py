@@ -33,7 +33,23 @@ SYMBOLS = (
     "ode_set_time_limit", "ode_set_launch", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
     "ode_solve", "ode_run_periods", "ode_synchronize", "ode_get_status", "ode_reset_counters",
     "ode_last_error", "ode_km_coefficients", "ode_kernel_info", "ode_probe_fma_peak",
+    "ode_run_periods_noalloc",
 )
+
+
+class NoAllocSettings(ctypes.Structure):
+    """Mirror of ``ode_noalloc_settings``."""
+
+    _fields_ = [
+        ("model", ctypes.c_int), ("scheme", ctypes.c_int), ("prec", ctypes.c_int),
+        ("rtol", ctypes.c_double * 4), ("atol", ctypes.c_double * 4),
+        ("h_max", ctypes.c_double), ("h_min", ctypes.c_double), ("grow_limit", ctypes.c_double),
+        ("shrink_limit", ctypes.c_double), ("events_enabled", ctypes.c_int),
+        ("direction", ctypes.c_int * 2), ("tolerance", ctypes.c_double * 2),
+        ("stop_count", ctypes.c_int * 2), ("max_steps_in_zone", ctypes.c_int),
+        ("time_domain_mode", ctypes.c_int), ("max_steps_per_slice", ctypes.c_longlong),
+        ("time_limit_s", ctypes.c_double), ("model_constants", ctypes.c_double * 8),
+    ]
 
 
 class ODEError(RuntimeError):
@@ -89,6 +105,8 @@ def load(build_if_missing: bool = True):
         "ode_km_coefficients": [d] * 13 + [_dp],
         "ode_kernel_info": [i, i, i, i, i, i, _ip, _ip, _ip],
         "ode_probe_fma_peak": [i, _dp, _dp],
+        "ode_run_periods_noalloc": [ctypes.POINTER(NoAllocSettings), i, i, d, i, i, _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_char_p)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -287,3 +305,25 @@ def ode_probe_fma_peak(device=0):
     d, f = ctypes.c_double(), ctypes.c_double()
     _check(load().ode_probe_fma_peak(device, ctypes.byref(d), ctypes.byref(f)))
     return d.value, f.value
+
+
+def ode_run_periods_noalloc(settings, n_systems, device, h0, n_transient, n_record, td, y, p, acc,
+                            records=None, status=None, accepted=None, stream=None):
+    """Integration on caller-owned device arrays with no device allocation
+    (see include/odegpu.h).  Arrays must be CUDA tensors (or device
+    pointers as ints)."""
+    def dev(x, dtype):
+        if x is None or isinstance(x, int):
+            return x
+        ptr, kind = _arr(x, dtype)
+        if kind != ODE_PTR_DEVICE:
+            raise ODEError(ODE_ERR_INVALID_ARG, "ode_run_periods_noalloc takes device arrays only")
+        return ptr
+    msg = ctypes.c_char_p()
+    rc = load().ode_run_periods_noalloc(
+        ctypes.byref(settings), n_systems, device, h0, n_transient, n_record, dev(td, np.float64),
+        dev(y, np.float64), dev(p, np.float64), dev(acc, np.float64), dev(records, np.float64),
+        dev(status, np.int32), dev(accepted, np.int64), _stream(stream), ctypes.byref(msg))
+    if rc != ODE_OK:
+        raise ODEError(rc, msg.value.decode() if msg.value else "")
+    return rc
