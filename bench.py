@@ -43,6 +43,10 @@ import workloads as W  # noqa: E402
 # (+ 6 sqrt).  Keller-Miksis RKCK45: 6 x 36 + 10 + 70 + 18 + 20 + 10 + 20 + 1
 # = 365 (+ 6 pow, 6 sincospi, 12 div).
 FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365}
+# transcendental calls per accepted step, converted to DFMA equivalents with
+# the library's call-cost probe (one DFMA = 2 flops) for the FMA-peak roofline
+TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {},
+                   "keller_miksis": {"pow": 6, "cos": 12}}
 METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
 UNIT = "system-steps/s"
 
@@ -189,6 +193,18 @@ def run_gpu(args):
         G.ode_linear_set(s, 0, 0, N, N, td=d_td, y=d_y0, p=d_p, acc=d_acc, copy_mode=G.ODE_ALL, stream=stream)
         G.ode_run_periods(s, w["h0"], n_tr, n_rec, d_rec, stream=stream)
 
+    tune = None
+    if args.autotune:
+        # the project's autotuner picks the launch shape on a short trial
+        G.ode_linear_set(s, 0, 0, N, N, td=d_td, y=d_y0, p=d_p, acc=d_acc, copy_mode=G.ODE_ALL, stream=stream)
+        bs, pers, trials = G.ode_autotune(s, w["h0"], args.tune_slices, stream)
+        tune = {"block": bs, "persistent": pers, "trial_slices": args.tune_slices,
+                "trial_ms": {"per_sweep": [round(x, 2) for x in trials[0]],
+                             "persistent": [round(x, 2) for x in trials[1]],
+                             "blocks": [64, 96, 128, 160, 192, 256]}}
+        args.persistent = pers
+        args.block = bs
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -250,9 +266,14 @@ def run_gpu(args):
     if not max_mhz:
         max_mhz = clk.get("sm_max_mhz") or 2070.0
     dfma, ffma = G.ode_probe_fma_peak(local)
+    cos_eq, pow_eq = G.ode_probe_call_cost(local)
     peak_tflops = 2 * 2 * sms * max_mhz * 1e6 / 1e12
-    flops = FLOPS_PER_STEP.get(args.workload, 0) * steps_per_pass
-    achieved_tflops = flops / (ms_step * 1e-3) / 1e12
+    arith = FLOPS_PER_STEP.get(args.workload, 0)
+    trans = TRANSCENDENTALS.get(args.workload, {})
+    eq = {"cos": cos_eq, "pow": pow_eq}
+    per_step = arith + sum(2.0 * eq[k] * v for k, v in trans.items())
+    achieved_tflops = per_step * steps_per_pass / (ms_step * 1e-3) / 1e12
+    achieved_arith = arith * steps_per_pass / (ms_step * 1e-3) / 1e12
 
     G.ode_destroy(s)
 
@@ -282,10 +303,14 @@ def run_gpu(args):
                     "s_per_step": float(np.mean(e2e_times)) if e2e_times else None},
             "gpu_launches": args.steps,  # one integrator launch per step
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "frac": achieved_tflops / peak_tflops, "traffic": args.traffic,
                          "peak_basis": "2 FP64 FMA/clk/SM x %d SMs x %.0f MHz x 2 (derived; live probe %.3f TFLOP/s)"
                                        % (sms, max_mhz, 2 * dfma / 1e12),
-                         "flops_per_step": FLOPS_PER_STEP.get(args.workload, 0)},
+                         "flops_per_step": per_step, "arith_flops_per_step": arith,
+                         "transcendentals_per_step": trans,
+                         "call_cost_dfma_equiv": {"cos": round(cos_eq, 2), "pow": round(pow_eq, 2)},
+                         "achieved_arith_only": achieved_arith, "frac_arith_only": achieved_arith / peak_tflops},
+            "launch": tune if tune else {"block": args.block, "persistent": args.persistent},
             "clocks": clk,
         }
         if not args.no_cpu_baseline and world == 1 or (world > 1 and not args.no_cpu_baseline):
@@ -363,6 +388,10 @@ def main():
                     choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis"])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--tune-slices", type=int, default=4)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch from an ncu capture of the same kernel (null if unknown)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

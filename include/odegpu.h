@@ -214,6 +214,18 @@ int ode_solve(ode_solver *s, double h0, void *stream);
 int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, double *records,
                     int ptr_kind, void *stream);
 
+/* Autotuner: integrate n_slices slices from the current state with every
+ * launch shape of a fixed candidate list -- block size 64, 96, 128, 160,
+ * 192, 256, each per-sweep and persistent (shapes the kernel cannot launch
+ * are skipped) -- timed with CUDA events on `stream`, then restore the state,
+ * status and counters and keep the fastest shape (as ode_set_launch would).
+ * Outputs (may be NULL): the chosen block size and persistent flag, and
+ * trial_ms[12] = milliseconds per trial in the order [persistent][block]
+ * (-1 for skipped shapes).  Allocates a temporary copy of the state.
+ * Synchronous. */
+int ode_autotune(ode_solver *s, double h0, int n_slices, void *stream, int *block_size,
+                 int *persistent, double *trial_ms);
+
 /* Wait for all work this solver enqueued. */
 int ode_synchronize(ode_solver *s);
 
@@ -247,6 +259,12 @@ int ode_kernel_info(int model, int scheme, int prec, int persistent, int block_s
  * microkernels over every SM (FMA per second; one FMA = 2 flops).  Used as
  * the roofline peak of the arithmetic-bound integrators. */
 int ode_probe_fma_peak(int device, double *dfma_per_s, double *ffma_per_s);
+
+/* Measured cost of one binary64 cos() and one pow() call, in DFMA
+ * equivalents (call throughput relative to the DFMA issue rate, with the loop
+ * overhead subtracted).  Used to count the transcendental calls of an
+ * algorithm in the FMA-peak roofline. */
+int ode_probe_call_cost(int device, double *cos_dfma, double *pow_dfma);
 
 /* ---- integration without allocation ---------------------------------------- */
 

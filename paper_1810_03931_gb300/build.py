@@ -22,6 +22,8 @@ LIB = os.path.join(HERE, "libodegpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "-I" + INCLUDE, "-I" + CSRC]
+# extra nvcc flags, e.g. "-DODEGPU_MAX_THREADS=128 -DODEGPU_MIN_BLOCKS=6" (launch bounds)
+EXTRA_ENV = "ODEGPU_NVCC_FLAGS"
 
 
 def nvcc() -> str:
@@ -35,12 +37,19 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _flags():
+    return NVCC_FLAGS + os.environ.get(EXTRA_ENV, "").split()
+
+
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
 def is_stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    stamp = LIB + ".flags"
+    if not os.path.exists(stamp) or open(stamp).read() != " ".join(_flags()):
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _deps())
@@ -56,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + _flags() + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
@@ -73,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
     os.replace(tmp, LIB)
+    with open(LIB + ".flags", "w") as f:
+        f.write(" ".join(_flags()))
     return LIB
 
 

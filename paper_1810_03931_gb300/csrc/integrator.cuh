@@ -48,12 +48,27 @@ template <>
 struct StageType<kFP32RHS> { using type = float; };
 
 // ---- harmonic forcing ------------------------------------------------------
-// cos d and sin d for |d| <= 0.1 from their Taylor series to degree 8 and 9
-// (the first omitted terms are below 3e-17 relative on that interval).
-__device__ __forceinline__ void small_angle(double d, double& cd, double& sd) {
-  const double u = d * d;
-  cd = fma(fma(fma(fma(u, 1.0 / 40320.0, -1.0 / 720.0), u, 1.0 / 24.0), u, -0.5), u, 1.0);
-  sd = d * fma(fma(fma(fma(u, 1.0 / 362880.0, -1.0 / 5040.0), u, 1.0 / 120.0), u, -1.0 / 6.0), u, 1.0);
+// For a stage at t + c h the forcing angle advances by c x with x = omega h.
+// cos(c x) and sin(c x) come from their Taylor series to degree 8 and 9 in x,
+// with the powers of c folded into compile-time coefficients, as polynomials
+// in U = x^2 (the first omitted terms are below 3e-17 relative for |x| <= 0.1):
+//   cos(c x) = 1 + U (a1 + U (a2 + U (a3 + U a4))),  a_k = (-1)^k c^2k / (2k)!
+//   sin(c x) = x (b0 + U (b1 + U (b2 + U (b3 + U b4)))), b_k = (-1)^k c^(2k+1) / (2k+1)!
+__host__ __device__ constexpr double cpow(double c, int k) { return k == 0 ? 1.0 : c * cpow(c, k - 1); }
+__host__ __device__ constexpr double fact(int k) { return k <= 1 ? 1.0 : k * fact(k - 1); }
+__host__ __device__ constexpr double cos_coef(double c, int k) { return (k % 2 ? -1.0 : 1.0) * cpow(c, 2 * k) / fact(2 * k); }
+__host__ __device__ constexpr double sin_coef(double c, int k) {
+  return (k % 2 ? -1.0 : 1.0) * cpow(c, 2 * k + 1) / fact(2 * k + 1);
+}
+
+template <int CNUM, int CDEN>
+__device__ __forceinline__ void small_angle_c(double x, double U, double& cd, double& sd) {
+  constexpr double c = (double)CNUM / (double)CDEN;
+  constexpr double a1 = cos_coef(c, 1), a2 = cos_coef(c, 2), a3 = cos_coef(c, 3), a4 = cos_coef(c, 4);
+  constexpr double b0 = sin_coef(c, 0), b1 = sin_coef(c, 1), b2 = sin_coef(c, 2), b3 = sin_coef(c, 3),
+                   b4 = sin_coef(c, 4);
+  cd = fma(fma(fma(fma(U, a4, a3), U, a2), U, a1), U, 1.0);
+  sd = x * fma(fma(fma(fma(U, b4, b3), U, b2), U, b1), U, b0);
 }
 
 constexpr double kSmallAngle = 0.1;
@@ -72,22 +87,27 @@ struct Stepper {
   using T = typename StageType<PREC>::type;
   static constexpr bool kRotate = (PREC == kFP64) && (M::kForcing != kNoForcing);
 
-  static __device__ __forceinline__ Stage<T> stage_at(double t, double hs, T tb, T h, double c,
+  // Stage time t + c hs with c = CNUM / CDEN; in binary64 the forcing
+  // (cos, sin)(omega (t + c hs)) follows from the anchor (C, S) by angle
+  // addition when |omega hs| <= 0.1 (x = omega hs, U = x^2 precomputed).
+  template <int CNUM, int CDEN>
+  static __device__ __forceinline__ Stage<T> stage_at(double t, double hs, T tb, T h,
                                                       const T (&mct)[3], double C, double S,
-                                                      double w) {
+                                                      double w, double x, double U, bool small) {
+    constexpr double c = (double)CNUM / (double)CDEN;
     Stage<T> st;
     if constexpr (kRotate) {
       st.t = t + c * hs;
-      const double d = w * (c * hs);
-      if (fabs(d) <= kSmallAngle) {
+      if (small) {
         double cd, sd;
-        small_angle(d, cd, sd);
+        small_angle_c<CNUM, CDEN>(x, U, cd, sd);
         st.c = C * cd - S * sd;
         st.s = S * cd + C * sd;
       } else {
         sincos(w * st.t, &st.s, &st.c);
       }
     } else {
+      (void)t; (void)hs; (void)C; (void)S; (void)w; (void)x; (void)U; (void)small;
       st.t = tb + (T)c * h;
       if constexpr (M::kForcing != kNoForcing) {
         sincos_t(M::omega(mct) * st.t, &st.s, &st.c);
@@ -108,25 +128,27 @@ struct Stepper {
     for (int m = 0; m < n; m++) yb[m] = (T)y[m];
     const T h = (T)hs;
     const T tb = (T)t;
+    const double x = w * hs, U = x * x;
+    const bool small = fabs(x) <= kSmallAngle;
     T ys[n];
     if constexpr (SCHEME == kRKCK45) {
       using namespace ck;
       T k2[n], k3[n], k4[n], k5[n], k6[n];
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a21 * k1[m]);
-      M::template rhs<T>(stage_at(t, hs, tb, h, c2, mct, C, S, w), ys, pt, mct, k2);
+      M::template rhs<T>(stage_at<1, 5>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k2);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a31 * k1[m] + (T)a32 * k2[m]);
-      M::template rhs<T>(stage_at(t, hs, tb, h, c3, mct, C, S, w), ys, pt, mct, k3);
+      M::template rhs<T>(stage_at<3, 10>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h, (T)a41 * k1[m] + (T)a42 * k2[m] + (T)a43 * k3[m]);
-      M::template rhs<T>(stage_at(t, hs, tb, h, c4, mct, C, S, w), ys, pt, mct, k4);
+      M::template rhs<T>(stage_at<3, 5>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k4);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a51 * k1[m] + (T)a52 * k2[m] + (T)a53 * k3[m] + (T)a54 * k4[m]);
-      const Stage<T> s5 = stage_at(t, hs, tb, h, c5, mct, C, S, w);
+      const Stage<T> s5 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small);
       M::template rhs<T>(s5, ys, pt, mct, k5);
       Cn = (double)s5.c;
       Sn = (double)s5.s;
@@ -135,7 +157,7 @@ struct Stepper {
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a61 * k1[m] + (T)a62 * k2[m] + (T)a63 * k3[m] + (T)a64 * k4[m] +
                           (T)a65 * k5[m]);
-      M::template rhs<T>(stage_at(t, hs, tb, h, c6, mct, C, S, w), ys, pt, mct, k6);
+      M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k6);
 #pragma unroll
       for (int m = 0; m < n; m++) {
         // binary64 state update and error estimate
@@ -148,7 +170,7 @@ struct Stepper {
     } else {
       T k2[n], k3[n], k4[n];
       const T half = (T)0.5;
-      const Stage<T> sh = stage_at(t, hs, tb, h, 0.5, mct, C, S, w);
+      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
       M::template rhs<T>(sh, ys, pt, mct, k2);
@@ -157,7 +179,7 @@ struct Stepper {
       M::template rhs<T>(sh, ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
-      const Stage<T> s4 = stage_at(t, hs, tb, h, 1.0, mct, C, S, w);
+      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small);
       M::template rhs<T>(s4, ys, pt, mct, k4);
       Cn = (double)s4.c;
       Sn = (double)s4.s;
@@ -434,7 +456,7 @@ struct Lane {
         st0.c = fC;
         st0.s = fS;
       } else {
-        st0 = St::stage_at(t, 0.0, (T)t, (T)0, 0.0, mct, 0.0, 0.0, 0.0);
+        st0 = St::template stage_at<0, 1>(t, 0.0, (T)t, (T)0, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
       }
       M::template rhs<T>(st0, yb, pt, mct, k1);
       k1ok = true;
@@ -583,9 +605,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// Launch bounds of the integrator kernels (build-time tunables: fewer
+// registers per thread let more systems be resident at once).
+#ifndef ODEGPU_MAX_THREADS
+#define ODEGPU_MAX_THREADS 256
+#endif
+#ifndef ODEGPU_MIN_BLOCKS
+#define ODEGPU_MIN_BLOCKS 1
+#endif
+
 // ---- the kernel --------------------------------------------------------------
 template <class M, int SCHEME, int PREC, bool PERSIST>
-__global__ void __launch_bounds__(256) ode_kernel(const KArgs a) {
+__global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS) ode_kernel(const KArgs a) {
   using L_t = Lane<M, SCHEME, PREC>;
   using T = typename L_t::T;
   L_t L;

@@ -680,6 +680,89 @@ int ode_reset_counters(ode_solver* s, void* stream) {
 
 const char* ode_last_error(const ode_solver* s) { return s ? s->err.c_str() : g_err.c_str(); }
 
+int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* block_size,
+                 int* persistent, double* trial_ms) {
+  if (check_solver(s)) return ODE_ERR_INVALID_ARG;
+  if (!(h0 > 0.0) || !isfinite(h0)) return fail(s, ODE_ERR_INVALID_ARG, "h0 must be finite and > 0");
+  if (n_slices < 1 || n_slices > 1000000) return fail(s, ODE_ERR_INVALID_ARG, "n_slices out of range");
+  static const int kBlocks[6] = {64, 96, 128, 160, 192, 256};
+  DeviceGuard g(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = (size_t)s->N;
+  // the trial runs change time domain, state, accessories, status, counters:
+  // save them and put them back afterwards
+  const size_t dbl = (2 + s->n + s->A) * N, ints = (1 + s->E) * N, lls = 2 * N;
+  char* save = nullptr;
+  CK_CUDA(s, cudaMalloc(&save, dbl * sizeof(double) + ints * sizeof(int) + lls * sizeof(long long)));
+  struct Piece {
+    void* p;
+    size_t bytes;
+  } pieces[] = {{s->d_td, 2 * N * sizeof(double)},     {s->d_y, s->n * N * sizeof(double)},
+                {s->d_acc, s->A * N * sizeof(double)},  {s->d_status, N * sizeof(int)},
+                {s->d_ecnt, s->E * N * sizeof(int)},    {s->d_nacc, N * sizeof(long long)},
+                {s->d_nrej, N * sizeof(long long)}};
+  auto copy_all = [&](bool to_save) -> cudaError_t {
+    size_t off = 0;
+    for (auto& pc : pieces) {
+      cudaError_t e = to_save ? cudaMemcpyAsync(save + off, pc.p, pc.bytes, cudaMemcpyDeviceToDevice, st)
+                              : cudaMemcpyAsync(pc.p, save + off, pc.bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+      off += pc.bytes;
+    }
+    return cudaSuccess;
+  };
+  cudaError_t e = copy_all(true);
+  const int old_block = s->block_size, old_pers = s->persistent;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best = 1e300;
+  int best_b = 128, best_p = 1, rc = ODE_OK;
+  int max_threads = 1024;
+  for (int pers = 0; pers < 2 && e == cudaSuccess && rc == ODE_OK; pers++) {
+    const void* fn = kernel_for(s->model, s->scheme, s->prec, pers);
+    cudaFuncAttributes at;
+    if (fn && cudaFuncGetAttributes(&at, fn) == cudaSuccess) max_threads = at.maxThreadsPerBlock;
+    for (int k = 0; k < 6 && e == cudaSuccess; k++) {
+      if (trial_ms) trial_ms[pers * 6 + k] = -1.0;
+      if (!fn || kBlocks[k] > max_threads) continue;
+      int bps = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlocks[k], 0) != cudaSuccess || bps < 1)
+        continue;
+      s->block_size = kBlocks[k];
+      s->persistent = pers;
+      if ((e = copy_all(false)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      if ((rc = integrate(s, h0, n_slices, n_slices, nullptr, stream)) != ODE_OK) break;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (trial_ms) trial_ms[pers * 6 + k] = ms;
+      if (ms < best) {
+        best = ms;
+        best_b = kBlocks[k];
+        best_p = pers;
+      }
+    }
+  }
+  if (e == cudaSuccess) e = copy_all(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (rc != ODE_OK || e != cudaSuccess) {
+    s->block_size = old_block;
+    s->persistent = old_pers;
+    return rc != ODE_OK ? rc : cuda_fail(s, e, "ode_autotune");
+  }
+  s->block_size = best_b;
+  s->persistent = best_p;
+  if (block_size) *block_size = best_b;
+  if (persistent) *persistent = best_p;
+  return check_watchdog(s, st);
+}
+
 int ode_km_coefficients(double PA1, double PA2, double omega1, double omega2, double theta,
                         double RE, double Pinf, double pV, double sigma, double mu, double rho,
                         double cL, double gamma, double* C) {

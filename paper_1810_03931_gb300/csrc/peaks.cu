@@ -47,7 +47,76 @@ cudaError_t time_chains(int sms, int iters, double* fma_per_s) {
   return e;
 }
 
+// Cost of a binary64 cos (and of a general pow) in units of the DFMA issue
+// rate: four independent accumulation chains per thread with and without the
+// call; the difference isolates the call.
+template <int KIND>
+__global__ void call_chains(double* out, int iters) {
+  double x0 = 0.1 + threadIdx.x * 1e-5, x1 = x0 + 1.5, x2 = x0 + 3.0, x3 = x0 + 4.5;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int i = 0; i < iters; i++) {
+    if (KIND == 1) {
+      s0 += cos(x0); s1 += cos(x1); s2 += cos(x2); s3 += cos(x3);
+    } else if (KIND == 2) {
+      s0 += pow(x0, -0.2); s1 += pow(x1, -0.2); s2 += pow(x2, -0.2); s3 += pow(x3, -0.2);
+    } else {
+      s0 += x0; s1 += x1; s2 += x2; s3 += x3;
+    }
+    x0 += 0.0123; x1 += 0.0123; x2 += 0.0123; x3 += 0.0123;
+    if (x0 > 6.0) x0 -= 5.9;
+    if (x1 > 6.0) x1 -= 5.9;
+    if (x2 > 6.0) x2 -= 5.9;
+    if (x3 > 6.0) x3 -= 5.9;
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s0 + s1 + s2 + s3;
+}
+
+template <int KIND>
+cudaError_t time_calls(int sms, int iters, double* seconds) {
+  const int threads = 256, blocks = sms * 4;
+  double* out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(double));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  call_chains<KIND><<<blocks, threads>>>(out, 4);
+  cudaEventRecord(e0);
+  call_chains<KIND><<<blocks, threads>>>(out, iters);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) *seconds = ms * 1e-3 / ((double)blocks * threads * iters * 4);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return e;
+}
+
 }  // namespace
+
+extern "C" int ode_probe_call_cost(int device, double* cos_dfma, double* pow_dfma) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return ODE_ERR_CUDA;
+  int sms = 0;
+  double dfma = 0, t_cos = 0, t_pow = 0, t_loop = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = time_chains<double>(sms, 1000, &dfma);
+  if (e == cudaSuccess) e = time_calls<1>(sms, 2000, &t_cos);
+  if (e == cudaSuccess) e = time_calls<2>(sms, 500, &t_pow);
+  if (e == cudaSuccess) e = time_calls<0>(sms, 2000, &t_loop);
+  // per-thread seconds per call -> DFMA issue slots of the whole GPU
+  const double threads = (double)sms * 4 * 256;
+  if (e == cudaSuccess) {
+    if (cos_dfma) *cos_dfma = (t_cos - t_loop) * dfma * threads;
+    if (pow_dfma) *pow_dfma = (t_pow - t_loop) * dfma * threads;
+  }
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? ODE_OK : ODE_ERR_CUDA;
+}
 
 extern "C" int ode_probe_fma_peak(int device, double* dfma_per_s, double* ffma_per_s) {
   int prev = -1;

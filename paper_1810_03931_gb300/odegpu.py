@@ -31,9 +31,9 @@ SYMBOLS = (
     "ode_create", "ode_destroy", "ode_query_dims", "ode_num_systems", "ode_set_tolerances",
     "ode_set_events", "ode_set_model_constants", "ode_set_time_domain_mode", "ode_set_step_budget",
     "ode_set_time_limit", "ode_set_launch", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
-    "ode_solve", "ode_run_periods", "ode_synchronize", "ode_get_status", "ode_reset_counters",
+    "ode_solve", "ode_run_periods", "ode_autotune", "ode_synchronize", "ode_get_status", "ode_reset_counters",
     "ode_last_error", "ode_km_coefficients", "ode_kernel_info", "ode_probe_fma_peak",
-    "ode_run_periods_noalloc",
+    "ode_probe_call_cost", "ode_run_periods_noalloc",
 )
 
 
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "ode_random_get": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
         "ode_solve": [_vp, d, _vp],
         "ode_run_periods": [_vp, d, i, i, _vp, i, _vp],
+        "ode_autotune": [_vp, d, i, _vp, _ip, _ip, _dp],
         "ode_synchronize": [_vp],
         "ode_get_status": [_vp, _vp, _vp, _vp, _vp, i, _vp],
         "ode_reset_counters": [_vp, _vp],
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
         "ode_km_coefficients": [d] * 13 + [_dp],
         "ode_kernel_info": [i, i, i, i, i, i, _ip, _ip, _ip],
         "ode_probe_fma_peak": [i, _dp, _dp],
+        "ode_probe_call_cost": [i, _dp, _dp],
         "ode_run_periods_noalloc": [ctypes.POINTER(NoAllocSettings), i, i, d, i, i, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_char_p)],
     }
@@ -270,6 +272,15 @@ def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
                                          ODE_PTR_HOST if kind is None else kind, _stream(stream)), s)
 
 
+def ode_autotune(s, h0, n_slices, stream=None):
+    """Returns (block_size, persistent, trial_ms[2][6])."""
+    b, p = ctypes.c_int(), ctypes.c_int()
+    t = np.zeros(12)
+    _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(p),
+                               t.ctypes.data_as(_dp)), s)
+    return b.value, p.value, t.reshape(2, 6)
+
+
 def ode_synchronize(s):
     return _check(load().ode_synchronize(s), s)
 
@@ -299,6 +310,12 @@ def ode_kernel_info(model, scheme, prec, persistent=0, block_size=0, device=0):
     _check(load().ode_kernel_info(model, scheme, prec, persistent, block_size, device, ctypes.byref(r),
                                   ctypes.byref(l), ctypes.byref(b)))
     return dict(regs=r.value, local_bytes=l.value, blocks_per_sm=b.value)
+
+
+def ode_probe_call_cost(device=0):
+    c, p = ctypes.c_double(), ctypes.c_double()
+    _check(load().ode_probe_call_cost(device, ctypes.byref(c), ctypes.byref(p)))
+    return c.value, p.value
 
 
 def ode_probe_fma_peak(device=0):

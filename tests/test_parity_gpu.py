@@ -432,6 +432,25 @@ def test_watchdog_stops_a_launch_that_runs_too_long():
             G.ode_destroy(s)
 
 
+def test_autotune_restores_state_and_keeps_results():
+    w = W.duffing_rkck(32, 4, 2, 2)
+    ref = run_gpu(w)
+    s = gpu_solver(w)
+    try:
+        gpu_load(s, w)
+        bs, pers, trials = G.ode_autotune(s, w["h0"], 2)
+        assert bs in (64, 96, 128, 160, 192, 256) and pers in (0, 1)
+        assert np.all(trials[trials >= 0] > 0) and trials.max() > 0
+        rec = np.zeros((2, 10, w["N"]))
+        G.ode_run_periods(s, w["h0"], 2, 2, rec)
+        G.ode_synchronize(s)
+        r = gpu_results(s, w, rec)
+        for key in ("records", "y", "acc", "nacc", "status"):
+            np.testing.assert_array_equal(r[key], ref[key])
+    finally:
+        G.ode_destroy(s)
+
+
 def test_kernels_do_not_spill():
     for model in (0, 1, 2, 3):
         for scheme in (0, 1):
