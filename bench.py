@@ -378,6 +378,93 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Serving mix: continuous batching of sweep requests
+# ---------------------------------------------------------------------------
+def run_serving(args):
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_1810_03931_gb300 import build as B
+    from paper_1810_03931_gb300 import odegpu as G
+    from _runners import DIMS, km_params_gpu
+    from test_serving_gpu import settings_for
+
+    B.build()
+    G.load(build_if_missing=False)
+    torch.cuda.set_device(0)
+    caps = {W.DUFFING: 1 << 17, W.VALVE: 1 << 16, W.KELLER_MIKSIS: 1 << 17}
+    base = {W.DUFFING: W.duffing_rkck(1, 1, 0, 1), W.VALVE: W.valve(1, 0, 1),
+            W.KELLER_MIKSIS: W.keller_miksis(1, 1, 0, 1)}
+
+    def server():
+        srv = G.ode_server_create(0, 8 << 30, args.slice_periods)
+        for m, w in base.items():
+            G.ode_server_add_model(srv, settings_for(w), w["h0"], caps[m])
+        return srv
+
+    reqs = W.serving_mix(args.requests, rate=1.0, max_log2_size=args.max_log2_size,
+                         max_log2_h=args.max_log2_horizon)
+    inputs = []
+    for r in reqs:
+        w = W.request_inputs(r)
+        p = km_params_gpu(w) if r["model"] == W.KELLER_MIKSIS else w["p"]
+        inputs.append((np.ascontiguousarray(w["td"]), np.ascontiguousarray(w["y0"]), np.ascontiguousarray(p)))
+
+    def drive(arrivals):
+        """Submit request k at arrivals[k] seconds; returns (makespan, latencies, steps)."""
+        srv = server()
+        try:
+            t0 = time.perf_counter()
+            pending, open_t, lat, steps = 0, {}, [], 0
+            k = 0
+            while k < len(reqs) or open_t:
+                now = time.perf_counter() - t0
+                while k < len(reqs) and arrivals[k] <= now:
+                    r = reqs[k]
+                    td, y0, p = inputs[k]
+                    t = G.ode_server_submit(srv, r["model"], r["horizon"], td, y0, p)
+                    open_t[t] = k
+                    k += 1
+                G.ode_server_progress(srv)
+                for t in list(open_t):
+                    if G.ode_server_poll(srv, t) == 2:
+                        r = reqs[open_t.pop(t)]
+                        n_sys, _, A, _ = DIMS[r["model"]]
+                        res = G.ode_server_result(srv, t, r["size"], n_sys, A)
+                        lat.append(res["latency"])
+                        steps += int(res["nacc"].sum())
+                if not open_t and k < len(reqs):
+                    time.sleep(max(0.0, min(0.01, arrivals[k] - (time.perf_counter() - t0))))
+                else:
+                    time.sleep(0.0002)
+            return time.perf_counter() - t0, np.array(lat), steps
+        finally:
+            G.ode_server_destroy(srv)
+
+    # sustained capacity: the whole mix submitted at once
+    span, lat0, steps0 = drive([0.0] * len(reqs))
+    capacity = len(reqs) / span
+    out = {"closed_batch": {"requests": len(reqs), "makespan_s": span, "steps_per_s": steps0 / span,
+                            "requests_per_s": capacity}}
+    unit_arrivals = np.array([r["arrival"] for r in reqs])  # rate 1 request/s
+    for frac in args.load_fracs:
+        lam = frac * capacity
+        span_f, lat, steps = drive(list(unit_arrivals / lam))
+        out["load_%.2f" % frac] = {"lambda_req_per_s": lam, "p50_latency_s": float(np.percentile(lat, 50)),
+                                   "p99_latency_s": float(np.percentile(lat, 99)),
+                                   "steps_per_s": steps / span_f, "makespan_s": span_f}
+    line = {"metric": "serving: accepted system-steps/s and p50/p99 request latency", "value": steps0 / span,
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving mix: Poisson stream over Duffing / Keller-Miksis / valve sweeps",
+                       "requests": len(reqs), "sizes": "floor(2^U(0,%d))" % args.max_log2_size,
+                       "horizons": "floor(2^U(4,%d)) periods" % args.max_log2_horizon,
+                       "slice_periods_per_tick": args.slice_periods, "pool_capacity": {
+                           "duffing": caps[W.DUFFING], "valve": caps[W.VALVE],
+                           "keller_miksis": caps[W.KELLER_MIKSIS]}},
+            "serving": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,7 +472,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="duffing_rkck",
-                    choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis"])
+                    choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "serving"])
+    ap.add_argument("--requests", type=int, default=60, help="serving: requests per run")
+    ap.add_argument("--slice-periods", type=int, default=8, help="serving: periods per tick")
+    ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
+    ap.add_argument("--max-log2-horizon", type=int, default=10, help="serving: horizons floor(2^U(4, x))")
+    ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 0.8, 1.0])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
@@ -400,6 +492,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

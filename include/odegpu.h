@@ -266,8 +266,6 @@ int ode_probe_fma_peak(int device, double *dfma_per_s, double *ffma_per_s);
  * algorithm in the FMA-peak roofline. */
 int ode_probe_call_cost(int device, double *cos_dfma, double *pow_dfma);
 
-/* ---- integration without allocation ---------------------------------------- */
-
 /* Settings of ode_run_periods_noalloc (host memory, read during the call).
  * rtol / atol: first n entries used; direction / tolerance / stop_count:
  * first E entries used (E, n of the model, see enum ode_model); the meaning
@@ -288,6 +286,59 @@ typedef struct ode_noalloc_settings {
     double time_limit_s;
     double model_constants[8];
 } ode_noalloc_settings;
+
+/* ---- serving: continuous batching of sweep requests (not in the paper) ---- */
+
+/* A request loop for parameter-sweep requests of uneven size, model and
+ * horizon.  Each served model has a resident pool of `capacity` system slots
+ * in HBM (the pools together must fit in the server's HBM budget: admission
+ * by footprint).  A request of n systems and n_periods periods waits (FIFO per
+ * model) until a contiguous range of n free slots exists, is then copied into
+ * it and stays resident there between ticks.  A tick integrates every occupied
+ * slot of a pool for up to slice_periods slices in one persistent launch
+ * (replayed as a CUDA graph on the pool's own stream; the pools of different
+ * models run concurrently).  When its horizon is done a request is copied out
+ * asynchronously and its slots are reused at once.  A request's results are
+ * those of ode_run_periods with n_transient = n_periods - 1, n_record = 1
+ * (same per-system arithmetic), alone or in any mix.
+ * The caller drives the loop with ode_server_progress (non-blocking). */
+typedef struct ode_server ode_server;
+
+/* device, HBM budget for the pools (bytes), slices per tick (>= 1). */
+int ode_server_create(ode_server **out, int device, long long hbm_budget_bytes, int slice_periods);
+
+/* Serve a model with the settings of ode_run_periods_noalloc (the settings'
+ * model / scheme / precision select the kernel), initial step h0 and a pool of
+ * `capacity` slots.  Errors: INVALID_ARG, OUT_OF_MEMORY (pool beyond the
+ * budget), CUDA. */
+int ode_server_add_model(ode_server *s, const ode_noalloc_settings *settings, double h0, int capacity);
+
+/* Queue a request: host arrays td [2][n], y0 [n_sys][n], p [P][n] (copied
+ * before return).  *ticket identifies it.  n must not exceed the pool. */
+int ode_server_submit(ode_server *s, int model, int n_systems, int n_periods, const double *td,
+                      const double *y0, const double *p, long long *ticket);
+
+/* One non-blocking pass of the loop: account completed ticks, copy out
+ * finished requests, admit waiting ones, launch the next ticks.  Outputs the
+ * numbers of resident and waiting requests (may be NULL). */
+int ode_server_progress(ode_server *s, int *n_running, int *n_waiting);
+
+/* State of a request: 0 waiting, 1 running, 2 done. */
+int ode_server_poll(ode_server *s, long long ticket, int *state);
+
+/* Results of a finished request (host arrays, any may be NULL): td [2][n],
+ * y [n_sys][n], accessories of its last period [A][n], status [n], accepted
+ * steps [n], and its latency (submit to results on the host, seconds).
+ * Releases the ticket.  NOT_READY if the request has not finished. */
+int ode_server_result(ode_server *s, long long ticket, double *td, double *y, double *acc,
+                      int *status, long long *accepted, double *latency_s);
+
+int ode_server_destroy(ode_server *s);
+const char *ode_server_last_error(const ode_server *s);
+
+/* ---- integration without allocation ---------------------------------------- */
+
+
 
 /* The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory themselves or through the library: code whose

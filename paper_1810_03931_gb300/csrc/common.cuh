@@ -61,6 +61,8 @@ struct KArgs {
   int n_slices;
   int n_skip;
   double h0;
+  int* slices_left;          // per-system slices still to run (served pools), or null:
+                             // a system runs min(n_slices, slices_left[i]) slices
   unsigned int* queue_head;  // persistent launches: next system to take
   int* flags;                // flags[0] != 0: the watchdog stopped a system
   long long time_limit_ns;   // per-thread run-time limit of one launch (0 = none)

@@ -238,6 +238,7 @@ struct Lane {
 
   int sys;
   int slice;
+  int my_slices;
   int status;
   bool k1ok;
   bool locating;
@@ -262,8 +263,12 @@ struct Lane {
   double fCn, fSn;  // the same at t + hs of the last normal trial step
   double w;         // forcing angular frequency
 
-  __device__ __forceinline__ void load(const KArgs& a) {
+  // Load the slot; false when the system has no slice to run in this launch.
+  __device__ __forceinline__ bool load(const KArgs& a) {
     const int N = a.N;
+    my_slices = a.n_slices;
+    if (a.slices_left != nullptr) my_slices = min(my_slices, a.slices_left[sys]);
+    if (my_slices <= 0) return false;
     t0 = a.td[sys];
     t1 = a.td[N + sys];
 #pragma unroll
@@ -276,6 +281,7 @@ struct Lane {
     slice = 0;
     nacc = 0;
     nrej = 0;
+    return true;
   }
 
   __device__ __forceinline__ void store(const KArgs& a) {
@@ -291,6 +297,7 @@ struct Lane {
     for (int j = 0; j < E; j++) a.ecnt[j * N + sys] = a.pr.events_on ? ecnt[j] : 0;
     a.nacc[sys] += nacc;
     a.nrej[sys] += nrej;
+    if (a.slices_left != nullptr) a.slices_left[sys] -= slice;
   }
 
   __device__ __forceinline__ void anchor_forcing() {
@@ -638,27 +645,33 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS) ode_ker
 
   // Resolve slice / system ends (also zero-length slices) until the lane has
   // a slice to integrate or no work at all.
+  auto next_system = [&]() {
+    if constexpr (PERSIST) {
+      L.sys = (int)atomicAdd(a.queue_head, 1u);
+      active = L.sys < a.N;
+      fresh = active;
+    } else {
+      active = false;
+    }
+  };
   auto settle = [&]() {
     while (active) {
       if (fresh) {
-        L.load(a);
-        L.begin_slice(a);
         fresh = false;
+        if (!L.load(a)) {  // nothing to run for this slot in this launch
+          next_system();
+          continue;
+        }
+        L.begin_slice(a);
       }
       if (L.status == kStNone) return;
       L.end_slice(a);
-      if (L.slice < a.n_slices) {
+      if (L.slice < L.my_slices) {
         L.begin_slice(a);
         continue;
       }
       L.store(a);
-      if constexpr (PERSIST) {
-        L.sys = (int)atomicAdd(a.queue_head, 1u);
-        active = L.sys < a.N;
-        fresh = active;
-      } else {
-        active = false;
-      }
+      next_system();
     }
   };
 

@@ -361,6 +361,7 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.n_slices = n_slices;
   a.n_skip = n_skip;
   a.h0 = h0;
+  a.slices_left = nullptr;
   a.queue_head = s->d_queue;
   a.flags = (int*)((char*)s->d_queue + 64);
   a.time_limit_ns = (long long)(s->time_limit_s * 1e9);

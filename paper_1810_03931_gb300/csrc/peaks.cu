@@ -108,11 +108,10 @@ extern "C" int ode_probe_call_cost(int device, double* cos_dfma, double* pow_dfm
   if (e == cudaSuccess) e = time_calls<1>(sms, 2000, &t_cos);
   if (e == cudaSuccess) e = time_calls<2>(sms, 500, &t_pow);
   if (e == cudaSuccess) e = time_calls<0>(sms, 2000, &t_loop);
-  // per-thread seconds per call -> DFMA issue slots of the whole GPU
-  const double threads = (double)sms * 4 * 256;
+  // GPU seconds per call (all threads together) x DFMA per second of the GPU
   if (e == cudaSuccess) {
-    if (cos_dfma) *cos_dfma = (t_cos - t_loop) * dfma * threads;
-    if (pow_dfma) *pow_dfma = (t_pow - t_loop) * dfma * threads;
+    if (cos_dfma) *cos_dfma = (t_cos - t_loop) * dfma;
+    if (pow_dfma) *pow_dfma = (t_pow - t_loop) * dfma;
   }
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   return e == cudaSuccess ? ODE_OK : ODE_ERR_CUDA;

@@ -1,0 +1,514 @@
+// server.cu -- continuous-batching request loop for parameter-sweep requests.
+//
+// Each model has a resident pool of system slots in HBM (its size chosen by
+// the caller within the server's HBM budget).  A request -- n systems of one
+// model, each integrated for a number of periods (slices) -- is admitted when
+// a contiguous range of free slots exists; its inputs are copied into the
+// range and its state stays resident in the pool between ticks.  A tick
+// integrates every occupied slot of a pool for up to `slice_periods` slices
+// in one launch of the persistent integrator (a per-slot count of remaining
+// slices lets requests with different horizons share the launch); the tick is
+// a CUDA graph (queue reset + kernel) replayed on the pool's own stream, so
+// the pools of different models run concurrently.  When a tick completes,
+// requests whose horizon is done are copied out asynchronously and their slots
+// are reused by waiting requests at once (stream order protects the copies).
+//
+// Each system's arithmetic does not depend on its slot, its neighbours or the
+// tick boundaries (every slice restarts from its own state), so a request's
+// results are the same alone and in any mix.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/odegpu.h"
+#include "common.cuh"
+
+using namespace odegpu;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+bool dims(int model, int* n, int* P, int* A, int* E) {
+  switch (model) {
+    case ODE_DUFFING: *n = 2; *P = 2; *A = 7; *E = 1; return true;
+    case ODE_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return true;
+    case ODE_VALVE: *n = 3; *P = 5; *A = 5; *E = 2; return true;
+    case ODE_BOUNCE: *n = 2; *P = 2; *A = 6; *E = 1; return true;
+    default: return false;
+  }
+}
+
+const void* kernel_of(int model, int scheme, int prec) {
+  switch (model) {
+    case ODE_DUFFING: return kernel_duffing(scheme, prec, 1);
+    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, 1);
+    case ODE_VALVE: return kernel_valve(scheme, prec, 1);
+    case ODE_BOUNCE: return kernel_bounce(scheme, prec, 1);
+    default: return nullptr;
+  }
+}
+
+__global__ void fill_int_kernel(int* p, int n, int v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+enum ReqState { kWaiting = 0, kRunning = 1, kDone = 2 };
+
+struct Request {
+  long long ticket = 0;
+  int model = 0;
+  int n = 0;
+  int periods = 0;
+  int scheduled = 0;  // periods enqueued in ticks so far
+  int off = -1;       // first slot
+  int state = kWaiting;
+  bool harvesting = false;
+  double t_submit = 0, t_done = 0;
+  // pinned host buffers: inputs [2 + n_sys + P][n], outputs
+  double* h_in = nullptr;
+  double* h_out = nullptr;  // td [2][n], y [n_sys][n], acc [A][n]
+  int* h_status = nullptr;
+  long long* h_acc_steps = nullptr;
+  cudaEvent_t done_ev = nullptr;
+};
+
+struct Pool {
+  bool on = false;
+  int model = 0, scheme = 0, prec = 0;
+  int n = 0, P = 0, A = 0, E = 0;
+  int cap = 0;
+  double h0 = 0;
+  Props pr;
+  double time_limit_s = 600;
+  double *td = nullptr, *y = nullptr, *p = nullptr, *acc = nullptr;
+  int *status = nullptr, *ecnt = nullptr, *left = nullptr;
+  long long *nacc = nullptr, *nrej = nullptr;
+  unsigned char* head = nullptr;  // queue head + watchdog flag
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t tick_ev = nullptr;
+  bool tick_inflight = false;
+  std::map<int, int> free_ranges;  // offset -> length
+  std::deque<Request*> waiting;
+  std::vector<Request*> running;
+  size_t bytes = 0;
+  long long ticks = 0;
+};
+
+}  // namespace
+
+struct ode_server {
+  int device = 0;
+  int slice_periods = 1;
+  long long budget = 0;
+  long long used = 0;
+  Pool pools[4];
+  std::map<long long, Request*> reqs;
+  long long next_ticket = 1;
+  std::string err;
+};
+
+namespace {
+
+int sfail(ode_server* s, int code, const std::string& m) {
+  if (s) s->err = m;
+  return code;
+}
+
+int scuda(ode_server* s, cudaError_t e, const char* where) {
+  return sfail(s, e == cudaErrorMemoryAllocation ? ODE_ERR_OUT_OF_MEMORY : ODE_ERR_CUDA,
+               std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SCK(s, call)                                        \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return scuda((s), e_, #call);    \
+  } while (0)
+
+size_t per_system_bytes(int n, int P, int A, int E) {
+  return sizeof(double) * (2 + n + P + A) + sizeof(int) * (2 + E) + 2 * sizeof(long long);
+}
+
+// first-fit range allocator over the pool's slots
+int take_range(Pool& pl, int len) {
+  for (auto it = pl.free_ranges.begin(); it != pl.free_ranges.end(); ++it) {
+    if (it->second >= len) {
+      const int off = it->first, rest = it->second - len;
+      pl.free_ranges.erase(it);
+      if (rest > 0) pl.free_ranges[off + len] = rest;
+      return off;
+    }
+  }
+  return -1;
+}
+
+void give_range(Pool& pl, int off, int len) {
+  auto it = pl.free_ranges.emplace(off, len).first;
+  auto nx = std::next(it);
+  if (nx != pl.free_ranges.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    pl.free_ranges.erase(nx);
+  }
+  if (it != pl.free_ranges.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      pl.free_ranges.erase(it);
+    }
+  }
+}
+
+// Build the tick graph of a pool: reset the work queue, run slice_periods
+// slices of every occupied slot.
+int build_graph(ode_server* s, Pool& pl) {
+  const void* fn = kernel_of(pl.model, pl.scheme, pl.prec);
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = pl.cap;
+  a.td = pl.td;
+  a.y = pl.y;
+  a.p = pl.p;
+  a.acc = pl.acc;
+  a.status = pl.status;
+  a.ecnt = pl.ecnt;
+  a.nacc = pl.nacc;
+  a.nrej = pl.nrej;
+  a.records = nullptr;
+  a.n_slices = s->slice_periods;
+  a.n_skip = s->slice_periods;
+  a.h0 = pl.h0;
+  a.slices_left = pl.left;
+  a.queue_head = (unsigned int*)pl.head;
+  a.flags = (int*)(pl.head + 64);
+  a.time_limit_ns = (long long)(pl.time_limit_s * 1e9);
+  a.pr = pl.pr;
+  int sms = 0, bps = 0;
+  const int block = 128;
+  SCK(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+  SCK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, 0));
+  if (bps < 1) return sfail(s, ODE_ERR_UNSUPPORTED, "kernel cannot be resident");
+  long long grid = (long long)bps * sms;
+  const long long need = (pl.cap + block - 1) / block;
+  if (grid > need) grid = need;
+  cudaGraph_t g = nullptr;
+  SCK(s, cudaStreamBeginCapture(pl.stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(pl.head, 0, sizeof(unsigned int), pl.stream);
+  void* args[] = {&a};
+  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, 0, pl.stream);
+  cudaError_t e2 = cudaStreamEndCapture(pl.stream, &g);
+  if (e != cudaSuccess) return scuda(s, e, "tick capture");
+  if (e2 != cudaSuccess) return scuda(s, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&pl.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return scuda(s, e, "cudaGraphInstantiate");
+  return ODE_OK;
+}
+
+void free_request(Request* r) {
+  if (r->h_in) cudaFreeHost(r->h_in);
+  if (r->h_out) cudaFreeHost(r->h_out);
+  if (r->h_status) cudaFreeHost(r->h_status);
+  if (r->h_acc_steps) cudaFreeHost(r->h_acc_steps);
+  if (r->done_ev) cudaEventDestroy(r->done_ev);
+  delete r;
+}
+
+// Copy a request's inputs into its slot range and arm its slice count.
+int admit(ode_server* s, Pool& pl, Request* r) {
+  const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
+  const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
+  const double* in = r->h_in;
+  SCK(s, cudaMemcpy2DAsync(pl.td + r->off, pitch, in, row, row, 2, cudaMemcpyHostToDevice, pl.stream));
+  SCK(s, cudaMemcpy2DAsync(pl.y + r->off, pitch, in + 2 * n, row, row, pl.n, cudaMemcpyHostToDevice,
+                           pl.stream));
+  SCK(s, cudaMemcpy2DAsync(pl.p + r->off, pitch, in + (2 + pl.n) * n, row, row, pl.P,
+                           cudaMemcpyHostToDevice, pl.stream));
+  SCK(s, cudaMemsetAsync(pl.nacc + r->off, 0, n * sizeof(long long), pl.stream));
+  SCK(s, cudaMemsetAsync(pl.nrej + r->off, 0, n * sizeof(long long), pl.stream));
+  fill_int_kernel<<<(r->n + 255) / 256 < 1024 ? (r->n + 255) / 256 : 1024, 256, 0, pl.stream>>>(
+      pl.left + r->off, r->n, r->periods);
+  SCK(s, cudaGetLastError());
+  r->state = kRunning;
+  r->scheduled = 0;
+  pl.running.push_back(r);
+  return ODE_OK;
+}
+
+// Copy a finished request's results out (after the tick, in stream order).
+int harvest(ode_server* s, Pool& pl, Request* r) {
+  const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
+  const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
+  double* out = r->h_out;
+  SCK(s, cudaMemcpy2DAsync(out, row, pl.td + r->off, pitch, row, 2, cudaMemcpyDeviceToHost, pl.stream));
+  SCK(s, cudaMemcpy2DAsync(out + 2 * n, row, pl.y + r->off, pitch, row, pl.n, cudaMemcpyDeviceToHost,
+                           pl.stream));
+  SCK(s, cudaMemcpy2DAsync(out + (2 + pl.n) * n, row, pl.acc + r->off, pitch, row, pl.A,
+                           cudaMemcpyDeviceToHost, pl.stream));
+  SCK(s, cudaMemcpyAsync(r->h_status, pl.status + r->off, n * sizeof(int), cudaMemcpyDeviceToHost,
+                         pl.stream));
+  SCK(s, cudaMemcpyAsync(r->h_acc_steps, pl.nacc + r->off, n * sizeof(long long),
+                         cudaMemcpyDeviceToHost, pl.stream));
+  SCK(s, cudaEventRecord(r->done_ev, pl.stream));
+  r->harvesting = true;
+  give_range(pl, r->off, r->n);
+  return ODE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ode_server_create(ode_server** out, int device, long long hbm_budget_bytes, int slice_periods) {
+  if (!out) return ODE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (hbm_budget_bytes <= 0 || slice_periods < 1) return ODE_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ODE_ERR_CUDA;
+  ode_server* s = new (std::nothrow) ode_server();
+  if (!s) return ODE_ERR_OUT_OF_MEMORY;
+  s->device = device;
+  s->budget = hbm_budget_bytes;
+  s->slice_periods = slice_periods;
+  *out = s;
+  return ODE_OK;
+}
+
+int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double h0, int capacity) {
+  if (!s) return ODE_ERR_INVALID_ARG;
+  if (!cfg) return sfail(s, ODE_ERR_INVALID_ARG, "settings are NULL");
+  int n, P, A, E;
+  if (!dims(cfg->model, &n, &P, &A, &E)) return sfail(s, ODE_ERR_INVALID_ARG, "unknown model");
+  Pool& pl = s->pools[cfg->model];
+  if (pl.on) return sfail(s, ODE_ERR_INVALID_ARG, "model already added");
+  const void* fn = kernel_of(cfg->model, cfg->scheme, cfg->prec);
+  if (!fn) return sfail(s, ODE_ERR_INVALID_ARG, "no kernel for this model / scheme / precision");
+  if (capacity < 1) return sfail(s, ODE_ERR_INVALID_ARG, "capacity must be >= 1");
+  if (!(h0 > 0.0)) return sfail(s, ODE_ERR_INVALID_ARG, "h0 must be > 0");
+  if (!(cfg->h_min > 0.0) || !(cfg->h_max >= cfg->h_min) || !(cfg->grow_limit >= 1.0) ||
+      !(cfg->grow_limit <= 1e4) || !(cfg->shrink_limit >= 1e-4) || !(cfg->shrink_limit <= 1.0) ||
+      cfg->max_steps_per_slice < 1)
+    return sfail(s, ODE_ERR_INVALID_ARG, "invalid step-size settings");
+  const size_t bytes = per_system_bytes(n, P, A, E) * (size_t)capacity + 256;
+  if (s->used + (long long)bytes > s->budget)
+    return sfail(s, ODE_ERR_OUT_OF_MEMORY, "pool does not fit in the server's HBM budget");
+  if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
+  pl.model = cfg->model;
+  pl.scheme = cfg->scheme;
+  pl.prec = cfg->prec;
+  pl.n = n;
+  pl.P = P;
+  pl.A = A;
+  pl.E = E;
+  pl.cap = capacity;
+  pl.h0 = h0;
+  pl.time_limit_s = cfg->time_limit_s;
+  Props& pr = pl.pr;
+  memset(&pr, 0, sizeof(pr));
+  for (int i = 0; i < kMaxN; i++) {
+    pr.rtol[i] = i < n ? cfg->rtol[i] : 1.0;
+    pr.atol[i] = i < n ? cfg->atol[i] : 1.0;
+  }
+  pr.hmax = cfg->h_max;
+  pr.hmin = cfg->h_min;
+  pr.grow = cfg->grow_limit;
+  pr.shrink = cfg->shrink_limit;
+  pr.err_grow = pow(0.9 / pr.grow, 5.0);
+  pr.err_shrink = pow(0.9 / pr.shrink, 5.0);
+  for (int j = 0; j < kMaxE; j++) {
+    pr.evt_dir[j] = j < E ? cfg->direction[j] : -1;
+    pr.evt_tol[j] = j < E ? cfg->tolerance[j] : 0.0;
+    pr.evt_stop[j] = j < E ? cfg->stop_count[j] : 0;
+  }
+  pr.max_eq = cfg->max_steps_in_zone;
+  pr.events_on = cfg->events_enabled ? 1 : 0;
+  pr.td_mode = cfg->time_domain_mode;
+  pr.max_steps = cfg->max_steps_per_slice;
+  for (int i = 0; i < kMaxMC; i++) pr.mc[i] = cfg->model_constants[i];
+  const size_t C = (size_t)capacity;
+  struct {
+    void** p;
+    size_t b;
+  } al[] = {{(void**)&pl.td, 2 * C * sizeof(double)},     {(void**)&pl.y, n * C * sizeof(double)},
+            {(void**)&pl.p, P * C * sizeof(double)},      {(void**)&pl.acc, A * C * sizeof(double)},
+            {(void**)&pl.status, C * sizeof(int)},         {(void**)&pl.ecnt, E * C * sizeof(int)},
+            {(void**)&pl.left, C * sizeof(int)},           {(void**)&pl.nacc, C * sizeof(long long)},
+            {(void**)&pl.nrej, C * sizeof(long long)},     {(void**)&pl.head, 256}};
+  for (auto& x : al) {
+    SCK(s, cudaMalloc(x.p, x.b));
+    SCK(s, cudaMemset(*x.p, 0, x.b));
+  }
+  SCK(s, cudaStreamCreateWithFlags(&pl.stream, cudaStreamNonBlocking));
+  SCK(s, cudaEventCreateWithFlags(&pl.tick_ev, cudaEventDisableTiming));
+  pl.free_ranges.clear();
+  pl.free_ranges[0] = capacity;
+  pl.bytes = bytes;
+  s->used += (long long)bytes;
+  pl.on = true;
+  if (int rc = build_graph(s, pl)) {
+    pl.on = false;
+    return rc;
+  }
+  return ODE_OK;
+}
+
+int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, const double* td,
+                      const double* y0, const double* p, long long* ticket) {
+  if (!s) return ODE_ERR_INVALID_ARG;
+  if (model < 0 || model > 3 || !s->pools[model].on)
+    return sfail(s, ODE_ERR_INVALID_ARG, "model not served (ode_server_add_model)");
+  Pool& pl = s->pools[model];
+  if (n_systems < 1 || n_systems > pl.cap)
+    return sfail(s, ODE_ERR_INVALID_ARG, "request size outside [1, pool capacity]");
+  if (n_periods < 1) return sfail(s, ODE_ERR_INVALID_ARG, "n_periods must be >= 1");
+  if (!td || !y0 || !p || !ticket) return sfail(s, ODE_ERR_INVALID_ARG, "NULL argument");
+  if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
+  Request* r = new (std::nothrow) Request();
+  if (!r) return sfail(s, ODE_ERR_OUT_OF_MEMORY, "host allocation failed");
+  r->model = model;
+  r->n = n_systems;
+  r->periods = n_periods;
+  const size_t n = (size_t)n_systems;
+  cudaError_t e = cudaMallocHost(&r->h_in, (2 + pl.n + pl.P) * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&r->h_out, (2 + pl.n + pl.A) * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&r->h_status, n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&r->h_acc_steps, n * sizeof(long long));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_request(r);
+    return scuda(s, e, "request buffers");
+  }
+  memcpy(r->h_in, td, 2 * n * sizeof(double));
+  memcpy(r->h_in + 2 * n, y0, pl.n * n * sizeof(double));
+  memcpy(r->h_in + (2 + pl.n) * n, p, pl.P * n * sizeof(double));
+  r->ticket = s->next_ticket++;
+  r->t_submit = now_s();
+  s->reqs[r->ticket] = r;
+  pl.waiting.push_back(r);
+  *ticket = r->ticket;
+  return ODE_OK;
+}
+
+int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
+  if (!s) return ODE_ERR_INVALID_ARG;
+  if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
+  int running = 0, waiting = 0;
+  for (Pool& pl : s->pools) {
+    if (!pl.on) continue;
+    // 1. a completed tick: account the periods it ran, copy out finished requests
+    if (pl.tick_inflight) {
+      cudaError_t q = cudaEventQuery(pl.tick_ev);
+      if (q == cudaSuccess) {
+        pl.tick_inflight = false;
+        std::vector<Request*> still;
+        for (Request* r : pl.running) {
+          if (r->scheduled >= r->periods) {
+            if (int rc = harvest(s, pl, r)) return rc;
+          } else {
+            still.push_back(r);
+          }
+        }
+        pl.running.swap(still);
+      } else if (q != cudaErrorNotReady) {
+        return scuda(s, q, "tick");
+      }
+    }
+    // 2. admit waiting requests in arrival order while slots are free
+    while (!pl.waiting.empty()) {
+      Request* r = pl.waiting.front();
+      const int off = take_range(pl, r->n);
+      if (off < 0) break;
+      r->off = off;
+      pl.waiting.pop_front();
+      if (int rc = admit(s, pl, r)) return rc;
+    }
+    // 3. next tick
+    if (!pl.tick_inflight && !pl.running.empty()) {
+      for (Request* r : pl.running) r->scheduled += s->slice_periods;
+      SCK(s, cudaGraphLaunch(pl.graph, pl.stream));
+      SCK(s, cudaEventRecord(pl.tick_ev, pl.stream));
+      pl.tick_inflight = true;
+      pl.ticks++;
+    }
+    running += (int)pl.running.size();
+    waiting += (int)pl.waiting.size();
+  }
+  // 4. requests whose results have arrived
+  for (auto& kv : s->reqs) {
+    Request* r = kv.second;
+    if (r->harvesting && r->state != kDone) {
+      cudaError_t q = cudaEventQuery(r->done_ev);
+      if (q == cudaSuccess) {
+        r->state = kDone;
+        r->t_done = now_s();
+      } else if (q != cudaErrorNotReady) {
+        return scuda(s, q, "harvest");
+      }
+    }
+  }
+  if (n_running) *n_running = running;
+  if (n_waiting) *n_waiting = waiting;
+  return ODE_OK;
+}
+
+int ode_server_poll(ode_server* s, long long ticket, int* state) {
+  if (!s || !state) return ODE_ERR_INVALID_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(s, ODE_ERR_INVALID_ARG, "unknown ticket");
+  *state = it->second->state;
+  return ODE_OK;
+}
+
+int ode_server_result(ode_server* s, long long ticket, double* td, double* y, double* acc,
+                      int* status, long long* accepted, double* latency_s) {
+  if (!s) return ODE_ERR_INVALID_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(s, ODE_ERR_INVALID_ARG, "unknown ticket");
+  Request* r = it->second;
+  if (r->state != kDone) return sfail(s, ODE_ERR_NOT_READY, "request not finished");
+  const Pool& pl = s->pools[r->model];
+  const size_t n = (size_t)r->n;
+  if (td) memcpy(td, r->h_out, 2 * n * sizeof(double));
+  if (y) memcpy(y, r->h_out + 2 * n, pl.n * n * sizeof(double));
+  if (acc) memcpy(acc, r->h_out + (2 + pl.n) * n, pl.A * n * sizeof(double));
+  if (status) memcpy(status, r->h_status, n * sizeof(int));
+  if (accepted) memcpy(accepted, r->h_acc_steps, n * sizeof(long long));
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  s->reqs.erase(it);
+  free_request(r);
+  return ODE_OK;
+}
+
+int ode_server_destroy(ode_server* s) {
+  if (!s) return ODE_OK;
+  cudaSetDevice(s->device);
+  for (Pool& pl : s->pools) {
+    if (pl.stream) cudaStreamSynchronize(pl.stream);
+  }
+  for (auto& kv : s->reqs) free_request(kv.second);
+  for (Pool& pl : s->pools) {
+    void* ptrs[] = {pl.td, pl.y, pl.p, pl.acc, pl.status, pl.ecnt, pl.left, pl.nacc, pl.nrej, pl.head};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    if (pl.graph) cudaGraphExecDestroy(pl.graph);
+    if (pl.tick_ev) cudaEventDestroy(pl.tick_ev);
+    if (pl.stream) cudaStreamDestroy(pl.stream);
+  }
+  delete s;
+  return ODE_OK;
+}
+
+const char* ode_server_last_error(const ode_server* s) { return s ? s->err.c_str() : ""; }
+
+}  // extern "C"

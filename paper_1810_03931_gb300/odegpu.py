@@ -34,6 +34,8 @@ SYMBOLS = (
     "ode_solve", "ode_run_periods", "ode_autotune", "ode_synchronize", "ode_get_status", "ode_reset_counters",
     "ode_last_error", "ode_km_coefficients", "ode_kernel_info", "ode_probe_fma_peak",
     "ode_probe_call_cost", "ode_run_periods_noalloc",
+    "ode_server_create", "ode_server_add_model", "ode_server_submit", "ode_server_progress",
+    "ode_server_poll", "ode_server_result", "ode_server_destroy", "ode_server_last_error",
 )
 
 
@@ -110,10 +112,21 @@ def load(build_if_missing: bool = True):
         "ode_run_periods_noalloc": [ctypes.POINTER(NoAllocSettings), i, i, d, i, i, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_char_p)],
     }
+    sp = ctypes.POINTER(NoAllocSettings)
+    sig.update({
+        "ode_server_create": [ctypes.POINTER(_vp), i, ll, i],
+        "ode_server_add_model": [_vp, sp, d, i],
+        "ode_server_submit": [_vp, i, i, i, _dp, _dp, _dp, ctypes.POINTER(ll)],
+        "ode_server_progress": [_vp, _ip, _ip],
+        "ode_server_poll": [_vp, ll, _ip],
+        "ode_server_result": [_vp, ll, _dp, _dp, _dp, _ip, _lp, _dp],
+        "ode_server_destroy": [_vp],
+        "ode_server_last_error": [_vp],
+    })
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "ode_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
     _lib = L
     return L
 
@@ -344,3 +357,63 @@ def ode_run_periods_noalloc(settings, n_systems, device, h0, n_transient, n_reco
     if rc != ODE_OK:
         raise ODEError(rc, msg.value.decode() if msg.value else "")
     return rc
+
+
+# ---- serving -------------------------------------------------------------------
+def _scheck(rc, s):
+    if rc != ODE_OK:
+        msg = load().ode_server_last_error(s) if s else b""
+        raise ODEError(rc, msg.decode() if msg else "server call failed")
+    return rc
+
+
+def ode_server_create(device, hbm_budget_bytes, slice_periods):
+    h = _vp()
+    _scheck(load().ode_server_create(ctypes.byref(h), device, int(hbm_budget_bytes), int(slice_periods)), None)
+    return h
+
+
+def ode_server_add_model(s, settings, h0, capacity):
+    return _scheck(load().ode_server_add_model(s, ctypes.byref(settings), h0, int(capacity)), s)
+
+
+def ode_server_submit(s, model, n_periods, td, y0, p):
+    td = np.ascontiguousarray(td, dtype=np.float64)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    t = ctypes.c_longlong()
+    _scheck(load().ode_server_submit(s, model, td.shape[1], int(n_periods), td.ctypes.data_as(_dp),
+                                     y0.ctypes.data_as(_dp), p.ctypes.data_as(_dp), ctypes.byref(t)), s)
+    return t.value
+
+
+def ode_server_progress(s):
+    r, w = ctypes.c_int(), ctypes.c_int()
+    _scheck(load().ode_server_progress(s, ctypes.byref(r), ctypes.byref(w)), s)
+    return r.value, w.value
+
+
+def ode_server_poll(s, ticket):
+    st = ctypes.c_int()
+    _scheck(load().ode_server_poll(s, ticket, ctypes.byref(st)), s)
+    return st.value
+
+
+def ode_server_result(s, ticket, n, n_sys, n_acc):
+    td, y, acc = np.zeros((2, n)), np.zeros((n_sys, n)), np.zeros((n_acc, n))
+    status = np.zeros(n, dtype=np.int32)
+    accepted = np.zeros(n, dtype=np.int64)
+    lat = ctypes.c_double()
+    _scheck(load().ode_server_result(s, ticket, td.ctypes.data_as(_dp), y.ctypes.data_as(_dp),
+                                     acc.ctypes.data_as(_dp), status.ctypes.data_as(_ip),
+                                     accepted.ctypes.data_as(_lp), ctypes.byref(lat)), s)
+    return dict(td=td, y=y, acc=acc, status=status, nacc=accepted, latency=lat.value)
+
+
+def ode_server_destroy(s):
+    return _scheck(load().ode_server_destroy(s), None)
+
+
+def ode_server_last_error(s):
+    m = load().ode_server_last_error(s)
+    return m.decode() if m else ""

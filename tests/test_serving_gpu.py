@@ -1,0 +1,122 @@
+"""Serving (continuous batching): a request's results are the same alone and
+in a mix of requests of other models, sizes and horizons that arrive while it
+is resident, and equal to a plain ode_run_periods of the same systems."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_1810_03931_gb300 import odegpu as G
+
+from _runners import DIMS, km_params_gpu, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def settings_for(w):
+    n, P, A, E = DIMS[w["model"]]
+    s = G.NoAllocSettings()
+    s.model, s.scheme, s.prec = w["model"], w["scheme"], G.ODE_FP64
+    for i in range(4):
+        s.rtol[i] = w["rtol"]
+        s.atol[i] = w["atol"]
+    s.h_max, s.h_min, s.grow_limit, s.shrink_limit = w["hmax"], w["hmin"], w["grow"], w["shrink"]
+    s.events_enabled = int(w["events_on"])
+    for j in range(min(E, 2)):
+        s.direction[j] = w["evt_dir"][j]
+        s.tolerance[j] = w["evt_tol"][j]
+        s.stop_count[j] = w["evt_stop"][j]
+    s.max_steps_in_zone = w["max_eq"]
+    s.time_domain_mode = w["td_mode"]
+    s.max_steps_per_slice = 10**9
+    s.time_limit_s = 300.0
+    for i, c in enumerate(w["mc"]):
+        s.model_constants[i] = c
+    return s
+
+
+def make_server(slice_periods=3):
+    srv = G.ode_server_create(0, 1 << 30, slice_periods)
+    G.ode_server_add_model(srv, settings_for(W.duffing_rkck(1, 1, 0, 1)), 1e-2, 4096)
+    G.ode_server_add_model(srv, settings_for(W.valve(1, 0, 1)), 1e-2, 4096)
+    G.ode_server_add_model(srv, settings_for(W.keller_miksis(1, 1, 0, 1)), 1e-2, 4096)
+    return srv
+
+
+def request(model, n, periods, seed):
+    w = W.request_inputs(dict(model=model, size=n, horizon=periods, seed=seed))
+    p = km_params_gpu(w) if model == W.KELLER_MIKSIS else w["p"]
+    return w, p
+
+
+def drain(srv, tickets, timeout=120.0):
+    t0 = time.time()
+    done = {}
+    while len(done) < len(tickets):
+        G.ode_server_progress(srv)
+        for t, (model, n) in tickets.items():
+            if t not in done and G.ode_server_poll(srv, t) == 2:
+                nsys, _, A, _ = DIMS[model]
+                done[t] = G.ode_server_result(srv, t, n, nsys, A)
+        assert time.time() - t0 < timeout
+        time.sleep(0.0005)
+    return done
+
+
+def test_request_alone_and_in_the_mix_are_identical():
+    wa, pa = request(W.DUFFING, 150, 7, seed=11)
+    srv = make_server()
+    try:
+        ta = G.ode_server_submit(srv, W.DUFFING, 7, wa["td"], wa["y0"], pa)
+        alone = drain(srv, {ta: (W.DUFFING, 150)})[ta]
+    finally:
+        G.ode_server_destroy(srv)
+    srv = make_server()
+    try:
+        tickets = {}
+        others = [(W.KELLER_MIKSIS, 40, 5, 1), (W.VALVE, 300, 4, 2), (W.DUFFING, 1000, 5, 3),
+                  (W.DUFFING, 3000, 2, 4), (W.VALVE, 77, 9, 5)]
+        for k, (m, n, h, sd) in enumerate(others):
+            w, p = request(m, n, h, sd)
+            tickets[G.ode_server_submit(srv, m, h, w["td"], w["y0"], p)] = (m, n)
+            if k == 2:  # the request arrives while others are resident
+                for _ in range(5):
+                    G.ode_server_progress(srv)
+                ta2 = G.ode_server_submit(srv, W.DUFFING, 7, wa["td"], wa["y0"], pa)
+                tickets[ta2] = (W.DUFFING, 150)
+        res = drain(srv, tickets)
+        mixed = res[ta2]
+    finally:
+        G.ode_server_destroy(srv)
+    for key in ("td", "y", "acc", "status", "nacc"):
+        np.testing.assert_array_equal(alone[key], mixed[key], err_msg=key)
+    # and the same as a plain iterated integration of those systems
+    w = dict(wa, p=pa, n_transient=6, n_record=1)
+    ref = run_gpu(w, persistent=1)
+    np.testing.assert_array_equal(mixed["y"], ref["y"])
+    np.testing.assert_array_equal(mixed["acc"], ref["acc"])
+    np.testing.assert_array_equal(mixed["nacc"], ref["nacc"])
+    assert mixed["latency"] > 0
+
+
+def test_admission_waits_for_slots_and_rejects_oversized_requests():
+    srv = G.ode_server_create(0, 1 << 30, 2)
+    try:
+        G.ode_server_add_model(srv, settings_for(W.duffing_rkck(1, 1, 0, 1)), 1e-2, 256)
+        w, p = request(W.DUFFING, 200, 3, 7)
+        t1 = G.ode_server_submit(srv, W.DUFFING, 3, w["td"], w["y0"], p)
+        t2 = G.ode_server_submit(srv, W.DUFFING, 3, w["td"], w["y0"], p)
+        G.ode_server_progress(srv)
+        # only one 200-system request fits in 256 slots: the other waits
+        assert G.ode_server_poll(srv, t1) == 1 and G.ode_server_poll(srv, t2) == 0
+        res = drain(srv, {t1: (W.DUFFING, 200), t2: (W.DUFFING, 200)})
+        for key in ("y", "acc", "nacc"):
+            np.testing.assert_array_equal(res[t1][key], res[t2][key])
+        big, pb = request(W.DUFFING, 300, 1, 8)
+        with pytest.raises(G.ODEError):
+            G.ode_server_submit(srv, W.DUFFING, 1, big["td"], big["y0"], pb)
+        with pytest.raises(G.ODEError):  # pool beyond the HBM budget
+            G.ode_server_add_model(srv, settings_for(W.valve(1, 0, 1)), 1e-2, 1 << 30)
+    finally:
+        G.ode_server_destroy(srv)
