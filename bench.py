@@ -168,7 +168,8 @@ def run_gpu(args):
     R = A + n + 1
     stream = torch.cuda.current_stream(dev)
 
-    s = G.ode_create(w["model"], w["scheme"], G.ODE_FP64, N, local)
+    prec = G.ODE_FP32_RHS if args.prec == "fp32rhs" else G.ODE_FP64
+    s = G.ode_create(w["model"], w["scheme"], prec, N, local)
     G.ode_set_tolerances(s, np.full(n, w["rtol"]), np.full(n, w["atol"]), w["hmax"], w["hmin"], w["grow"],
                          w["shrink"])
     G.ode_set_events(s, int(w["events_on"]), np.array(w["evt_dir"][:E], dtype=np.int32),
@@ -296,7 +297,8 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32 rhs / f64 state",
+            "data": "synthetic",
             "config": describe(w, args.persistent, "flushed before every timed step (256 MB write)"),
             "accepted_steps_per_pass": steps_per_pass, "wall_s_timed": wall,
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -478,6 +480,7 @@ def main():
     ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
     ap.add_argument("--max-log2-horizon", type=int, default=10, help="serving: horizons floor(2^U(4, x))")
     ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 0.8, 1.0])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32rhs"])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
