@@ -111,6 +111,46 @@ def lib():
     return _lib
 
 
+class use_library:
+    """Context manager: route every oracle call through another build of the
+    oracle (tests compile deliberately broken copies to show that the pins
+    catch them)."""
+
+    def __init__(self, path):
+        self.path = path
+        self.saved = None
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        L = ctypes.CDLL(self.path)
+        for name in ("orc_dims", "orc_run", "orc_trace_slice", "orc_single_step", "orc_rhs",
+                     "orc_ck_tableau", "orc_rk4_tableau", "orc_km_coefficients"):
+            getattr(L, name).argtypes = getattr(self.saved, name).argtypes
+        _lib = L
+        return L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def build_variant(source_text, out_path):
+    """Compile a modified oracle source into `out_path` (tests only)."""
+    src = out_path[:-3] + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+                    "-D_GNU_SOURCE", "-o", out_path, src, "-lm", "-lpthread"], check=True)
+    return out_path
+
+
+def source():
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
 

@@ -32,6 +32,41 @@ struct Stage {
 
 enum Forcing { kNoForcing = 0, kCosForcing = 1, kSinCosForcing = 2 };
 
+// x^(-1/5) for x > 0: binary32 seed refined by two binary64 Newton steps for
+// z^-5 = x (z <- z + z (1 - x z^5) / 5; the error goes ~2e-7 -> ~1e-13 ->
+// rounding).
+__device__ __forceinline__ double rfifth_root(double x) {
+  double z = (double)exp2f(-0.2f * __log2f((float)x));
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const double z2 = z * z;
+    z = fma(0.2 * z, fma(-x, z2 * z2 * z, 1.0), z);
+  }
+  return z;
+}
+
+// rx^e with rx = 1 / x for the polytropic exponent e = 3 gamma.  When 5 e is a
+// small integer k (gamma = 1, 1.4 or 5/3 give k = 15, 21, 25) this is
+// rx^(k div 5) * (x^(-1/5))^(k mod 5): a few multiplications and one
+// Newton-refined fifth root instead of a general pow().  Other exponents,
+// and arguments outside the binary32 seed's range, take pow().
+__device__ __forceinline__ double polytropic_pow(double x, double rx, double e) {
+  const double k5 = 5.0 * e;
+  if (k5 == rint(k5) && k5 >= 0.0 && k5 <= 60.0 && x > 1e-30 && x < 1e30) {
+    const int k = (int)k5, q = k / 5, r = k % 5;
+    double v = 1.0;
+    for (int i = 0; i < q; i++) v *= rx;
+    if (r) {
+      const double f = rfifth_root(x);
+      double fr = f;
+      for (int i = 1; i < r; i++) fr *= f;
+      v *= fr;
+    }
+    return v;
+  }
+  return pow(rx, e);
+}
+
 // Ordinary accessories shared by all models (Sec. 6.7): running maximum and
 // minimum of y1 over accepted points, with their times.
 __device__ __forceinline__ void acc_minmax(double t, double y1, double* a) {
@@ -102,7 +137,7 @@ struct KellerMiksis {
     double s2 = 0.0, c2 = 0.0;
     if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * st.t + C[12], &s2, &c2);
     const double one_c9y2 = 1.0 + C[9] * y2;
-    const double num = (C[0] + C[1] * y2) * pow(rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
+    const double num = (C[0] + C[1] * y2) * polytropic_pow(y1, rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
                        C[4] * y2 * rx - (1.0 - C[9] * y2 * (1.0 / 3.0)) * 1.5 * y2 * y2 -
                        (C[5] * s1 + C[6] * s2) * one_c9y2 - y1 * (C[7] * c1 + C[8] * c2);
     const double den = y1 - C[9] * y1 * y2 + C[4] * C[9];

@@ -294,9 +294,11 @@ def test_event_inside_zone_at_start_is_not_detected():
     """A trajectory starting at a local maximum (y2 = 0) is in the leaving
     state; the first detection is the next maximum (Sec. 4, Sec. 7.2)."""
     cfg = O.make_config(O.DUFFING, O.RKCK45, 1e-2, events_on=True, evt_dir=(-1,), evt_tol=(1e-6,))
-    tr = O.trace_slice(cfg, [0.0, 4 * math.pi], [1.0, 0.0], [0.25, 0.3])
-    assert len(tr["ev_t"]) >= 1
-    assert tr["ev_t"][0] > 1.0
+    # exactly at the maximum, and inside the zone just before it (y2 > 0)
+    for y2 in (0.0, 5e-7):
+        tr = O.trace_slice(cfg, [0.0, 4 * math.pi], [1.0, y2], [0.25, 0.3])
+        assert len(tr["ev_t"]) >= 1
+        assert tr["ev_t"][0] > 1.0
 
 
 def test_wrong_direction_crossings_are_ignored():
