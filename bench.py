@@ -53,11 +53,7 @@ UNIT = "system-steps/s"
 
 def workload(name, rank=0):
     if name == "duffing_rkck":
-        w = W.duffing_rkck()
-        # weak scaling: rank r sweeps its own band of B above the base grid
-        w["p"] = w["p"].copy()
-        w["p"][1] += 0.2 * rank
-        return w
+        return rank_band(W.duffing_rkck(), rank)
     if name == "duffing_rk4":
         return W.duffing_rk4()
     if name == "valve":
@@ -129,6 +125,35 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# multi-rank aggregation (weak scaling: every rank integrates its own sweep)
+# ---------------------------------------------------------------------------
+def rank_band(w, rank):
+    """Weak scaling: rank r sweeps the base grid of B shifted up by 0.25 r, so
+    ranks never integrate the same system."""
+    w = dict(w)
+    w["p"] = w["p"].copy()
+    w["p"][1] += 0.25 * rank
+    return w
+
+
+def reduce_over_ranks(steps, ms, e2e_steps, e2e_s, world, device):
+    """Whole-job numbers: (sum of accepted steps, max time in ms, end-to-end
+    rate = sum of steps / max end-to-end time).  One collective per quantity
+    on the timing path only; the integration itself has no collective."""
+    e2e_rate = (e2e_steps / e2e_s) if e2e_s > 0 else None
+    if world <= 1:
+        return steps, ms, e2e_rate
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([steps, e2e_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    m = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    e2e_rate = float(t[1]) / float(m[1]) if float(m[1]) > 0 else None
+    return float(t[0]), float(m[0]), e2e_rate
 
 
 # ---------------------------------------------------------------------------
@@ -279,17 +304,9 @@ def run_gpu(args):
     G.ode_destroy(s)
 
     # aggregate over ranks: total accepted steps / max time
-    tot_steps, max_ms = steps_per_pass, ms_step
-    e2e_rate = float(np.mean(e2e_steps)) / float(np.mean(e2e_times)) if e2e_times else None
-    if world > 1:
-        t = torch.tensor([tot_steps, 0.0], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        m = torch.tensor([max_ms, float(np.mean(e2e_times)) if e2e_times else 0.0], dtype=torch.float64,
-                         device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        tot_steps, max_ms = float(t[0]), float(m[0])
-        if e2e_times:
-            e2e_rate = float(np.mean(e2e_steps)) * world / float(m[1])
+    tot_steps, max_ms, e2e_rate = reduce_over_ranks(
+        steps_per_pass, ms_step, float(np.mean(e2e_steps)) if e2e_steps else 0.0,
+        float(np.mean(e2e_times)) if e2e_times else 0.0, world, dev)
 
     line = None
     if rank == 0:
