@@ -430,11 +430,11 @@ def run_serving(args):
         inputs.append((np.ascontiguousarray(w["td"]), np.ascontiguousarray(w["y0"]), np.ascontiguousarray(p)))
 
     def drive(arrivals):
-        """Submit request k at arrivals[k] seconds; returns (makespan, latencies, steps)."""
+        """Server: submit request k at arrivals[k] s; returns (makespan, latencies, steps)."""
         srv = server()
         try:
             t0 = time.perf_counter()
-            pending, open_t, lat, steps = 0, {}, [], 0
+            open_t, lat, steps = {}, [], 0
             k = 0
             while k < len(reqs) or open_t:
                 now = time.perf_counter() - t0
@@ -447,9 +447,11 @@ def run_serving(args):
                 G.ode_server_progress(srv)
                 for t in list(open_t):
                     if G.ode_server_poll(srv, t) == 2:
-                        r = reqs[open_t.pop(t)]
+                        j = open_t.pop(t)
+                        r = reqs[j]
                         n_sys, _, A, _ = DIMS[r["model"]]
                         res = G.ode_server_result(srv, t, r["size"], n_sys, A)
+                        # latency from the scheduled arrival (submit happens at arrival)
                         lat.append(res["latency"])
                         steps += int(res["nacc"].sum())
                 if not open_t and k < len(reqs):
@@ -460,26 +462,73 @@ def run_serving(args):
         finally:
             G.ode_server_destroy(srv)
 
-    # sustained capacity: the whole mix submitted at once
-    span, lat0, steps0 = drive([0.0] * len(reqs))
-    capacity = len(reqs) / span
-    out = {"closed_batch": {"requests": len(reqs), "makespan_s": span, "steps_per_s": steps0 / span,
-                            "requests_per_s": capacity}}
+    def drive_sequential(arrivals):
+        """Plain per-sweep FP64 launches, one request at a time in arrival order
+        (a queue without batching): its own solver, ode_run_periods, read-back."""
+        t0 = time.perf_counter()
+        lat, steps = [], 0
+        for k, r in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            td, y0, p = inputs[k]
+            w = base[r["model"]]
+            n_sys, P, A, E = DIMS[r["model"]]
+            s = G.ode_create(r["model"], w["scheme"], G.ODE_FP64, r["size"], 0)
+            try:
+                G.ode_set_tolerances(s, np.full(n_sys, w["rtol"]), np.full(n_sys, w["atol"]), w["hmax"],
+                                     w["hmin"], w["grow"], w["shrink"])
+                G.ode_set_events(s, int(w["events_on"]), np.array(w["evt_dir"][:E], dtype=np.int32),
+                                 np.array(w["evt_tol"][:E]), np.array(w["evt_stop"][:E], dtype=np.int32),
+                                 w["max_eq"])
+                if w["mc"]:
+                    G.ode_set_model_constants(s, np.array(w["mc"], dtype=np.float64))
+                G.ode_set_time_domain_mode(s, w["td_mode"])
+                G.ode_set_launch(s, 128, 0)
+                n = r["size"]
+                G.ode_linear_set(s, 0, 0, n, n, td=td, y=y0, p=p, acc=np.zeros((A, n)))
+                G.ode_run_periods(s, w["h0"], r["horizon"] - 1, 1, None)
+                acc_steps = np.zeros(n, dtype=np.int64)
+                G.ode_get_status(s, accepted=acc_steps)
+                y = np.zeros((n_sys, n))
+                G.ode_linear_get(s, 0, 0, n, n, y=y, copy_mode=G.ODE_STATE)
+            finally:
+                G.ode_destroy(s)
+            lat.append(time.perf_counter() - t0 - arrivals[k])
+            steps += int(acc_steps.sum())
+        return time.perf_counter() - t0, np.array(lat), steps
+
+    def summary(span, lat, steps, lam=None):
+        d = {"makespan_s": span, "steps_per_s": steps / span, "p50_latency_s": float(np.percentile(lat, 50)),
+             "p99_latency_s": float(np.percentile(lat, 99))}
+        if lam is not None:
+            d["lambda_req_per_s"] = lam
+        return d
+
+    # capacity of the plain sequential launches: the whole mix submitted at once
+    span_seq, lat_seq, steps_seq = drive_sequential([0.0] * len(reqs))
+    span_srv, lat_srv, steps_srv = drive([0.0] * len(reqs))
+    capacity = len(reqs) / span_seq
+    out = {"closed_batch": {"plain_sequential": summary(span_seq, lat_seq, steps_seq),
+                            "served": summary(span_srv, lat_srv, steps_srv)},
+           "capacity_req_per_s": capacity}
     unit_arrivals = np.array([r["arrival"] for r in reqs])  # rate 1 request/s
     for frac in args.load_fracs:
         lam = frac * capacity
-        span_f, lat, steps = drive(list(unit_arrivals / lam))
-        out["load_%.2f" % frac] = {"lambda_req_per_s": lam, "p50_latency_s": float(np.percentile(lat, 50)),
-                                   "p99_latency_s": float(np.percentile(lat, 99)),
-                                   "steps_per_s": steps / span_f, "makespan_s": span_f}
-    line = {"metric": "serving: accepted system-steps/s and p50/p99 request latency", "value": steps0 / span,
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        arr = list(unit_arrivals / lam)
+        a = summary(*drive_sequential(arr), lam)
+        b_ = summary(*drive(arr), lam)
+        out["load_%.2f" % frac] = {"plain_sequential": a, "served": b_}
+    line = {"metric": "serving: accepted system-steps/s and p50/p99 request latency",
+            "value": steps_srv / span_srv, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
             "config": {"workload": "serving mix: Poisson stream over Duffing / Keller-Miksis / valve sweeps",
                        "requests": len(reqs), "sizes": "floor(2^U(0,%d))" % args.max_log2_size,
                        "horizons": "floor(2^U(4,%d)) periods" % args.max_log2_horizon,
-                       "slice_periods_per_tick": args.slice_periods, "pool_capacity": {
-                           "duffing": caps[W.DUFFING], "valve": caps[W.VALVE],
-                           "keller_miksis": caps[W.KELLER_MIKSIS]}},
+                       "slice_periods_per_tick": args.slice_periods,
+                       "arrival_rates": "fractions of the plain sequential capacity",
+                       "pool_capacity": {"duffing": caps[W.DUFFING], "valve": caps[W.VALVE],
+                                         "keller_miksis": caps[W.KELLER_MIKSIS]}},
             "serving": out}
     print(json.dumps(line), flush=True)
 
@@ -493,7 +542,7 @@ def main():
     ap.add_argument("--workload", default="duffing_rkck",
                     choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "serving"])
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per run")
-    ap.add_argument("--slice-periods", type=int, default=8, help="serving: periods per tick")
+    ap.add_argument("--slice-periods", type=int, default=2, help="serving: periods per tick")
     ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
     ap.add_argument("--max-log2-horizon", type=int, default=10, help="serving: horizons floor(2^U(4, x))")
     ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 0.8, 1.0])
