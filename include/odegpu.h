@@ -294,17 +294,18 @@ typedef struct ode_noalloc_settings {
  * in HBM (the pools together must fit in the server's HBM budget: admission
  * by footprint).  A request of n systems and n_periods periods waits (FIFO per
  * model) until a contiguous range of n free slots exists, is then copied into
- * it and stays resident there between ticks.  A tick integrates every occupied
- * slot of a pool for up to slice_periods slices in one persistent launch
- * (replayed as a CUDA graph on the pool's own stream; the pools of different
- * models run concurrently).  When its horizon is done a request is copied out
+ * it and stays resident there.  It advances in chunks of slice_periods slices,
+ * each one launch over its slot range (a CUDA graph captured at admission and
+ * replayed) on one of the server's streams; chunks of different requests and
+ * models run concurrently and a request's next chunk starts as soon as its
+ * previous one completes.  When its horizon is done a request is copied out
  * asynchronously and its slots are reused at once.  A request's results are
  * those of ode_run_periods with n_transient = n_periods - 1, n_record = 1
  * (same per-system arithmetic), alone or in any mix.
  * The caller drives the loop with ode_server_progress (non-blocking). */
 typedef struct ode_server ode_server;
 
-/* device, HBM budget for the pools (bytes), slices per tick (>= 1). */
+/* device, HBM budget for the pools (bytes), slices per chunk (>= 1). */
 int ode_server_create(ode_server **out, int device, long long hbm_budget_bytes, int slice_periods);
 
 /* Serve a model with the settings of ode_run_periods_noalloc (the settings'
@@ -318,8 +319,8 @@ int ode_server_add_model(ode_server *s, const ode_noalloc_settings *settings, do
 int ode_server_submit(ode_server *s, int model, int n_systems, int n_periods, const double *td,
                       const double *y0, const double *p, long long *ticket);
 
-/* One non-blocking pass of the loop: account completed ticks, copy out
- * finished requests, admit waiting ones, launch the next ticks.  Outputs the
+/* One non-blocking pass of the loop: launch the next chunk of every request
+ * whose chunk completed, copy out finished requests, admit waiting ones.  Outputs the
  * numbers of resident and waiting requests (may be NULL). */
 int ode_server_progress(ode_server *s, int *n_running, int *n_waiting);
 

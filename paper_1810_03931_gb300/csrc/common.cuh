@@ -48,7 +48,8 @@ struct Props {
 // Everything one integration launch needs.  All arrays are device pointers,
 // component-major with stride N (value[c * N + i]).
 struct KArgs {
-  int N;
+  int N;             // systems in this launch
+  int ld;            // stride between components of the per-system arrays (>= N)
   double* td;        // [2][N]  (t0, t1)
   double* y;         // [n][N]
   const double* p;   // [P][N]

@@ -265,7 +265,7 @@ struct Lane {
 
   // Load the slot; false when the system has no slice to run in this launch.
   __device__ __forceinline__ bool load(const KArgs& a) {
-    const int N = a.N;
+    const int N = a.ld;
     my_slices = a.n_slices;
     if (a.slices_left != nullptr) my_slices = min(my_slices, a.slices_left[sys]);
     if (my_slices <= 0) return false;
@@ -285,7 +285,7 @@ struct Lane {
   }
 
   __device__ __forceinline__ void store(const KArgs& a) {
-    const int N = a.N;
+    const int N = a.ld;
     a.td[sys] = t0;
     a.td[N + sys] = t1;
 #pragma unroll

@@ -51,8 +51,10 @@ __device__ __forceinline__ double rfifth_root(double x) {
 // Newton-refined fifth root instead of a general pow().  Other exponents,
 // and arguments outside the binary32 seed's range, take pow().
 __device__ __forceinline__ double polytropic_pow(double x, double rx, double e) {
+  // 5 e within rounding of an integer (3 * 1.4 is 4.1999999999999993 in
+  // binary64): the exponent is then taken as that integer over 5
   const double k5 = 5.0 * e;
-  if (k5 == rint(k5) && k5 >= 0.0 && k5 <= 60.0 && x > 1e-30 && x < 1e30) {
+  if (fabs(k5 - rint(k5)) <= 1e-12 * k5 && k5 >= 0.0 && k5 <= 60.0 && x > 1e-30 && x < 1e30) {
     const int k = (int)k5, q = k / 5, r = k % 5;
     double v = 1.0;
     for (int i = 0; i < q; i++) v *= rx;

@@ -170,6 +170,7 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   KArgs a;
   memset(&a, 0, sizeof(a));
   a.N = n_systems;
+  a.ld = n_systems;
   a.td = td;
   a.y = y;
   a.p = p;

@@ -349,6 +349,7 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   cudaStream_t st = (cudaStream_t)stream;
   KArgs a;
   a.N = s->N;
+  a.ld = s->N;
   a.td = s->d_td;
   a.y = s->d_y;
   a.p = s->d_p;

@@ -4,17 +4,18 @@
 // the caller within the server's HBM budget).  A request -- n systems of one
 // model, each integrated for a number of periods (slices) -- is admitted when
 // a contiguous range of free slots exists; its inputs are copied into the
-// range and its state stays resident in the pool between ticks.  A tick
-// integrates every occupied slot of a pool for up to `slice_periods` slices
-// in one launch of the persistent integrator (a per-slot count of remaining
-// slices lets requests with different horizons share the launch); the tick is
-// a CUDA graph (queue reset + kernel) replayed on the pool's own stream, so
-// the pools of different models run concurrently.  When a tick completes,
-// requests whose horizon is done are copied out asynchronously and their slots
-// are reused by waiting requests at once (stream order protects the copies).
+// range and its state stays resident there until its horizon is done.  An
+// admitted request advances in chunks of `slice_periods` slices: each chunk is
+// one launch of the integrator over the request's slot range (captured once as
+// a CUDA graph at admission and replayed), on one of the server's streams.
+// Chunks of different requests and models run concurrently on the device; a
+// request's next chunk is launched as soon as its previous chunk completes,
+// so requests never wait for each other's slow systems.  A finished request is
+// copied out asynchronously on its stream and its slots are reused at once
+// (stream order keeps the copy ahead of any later use of those slots).
 //
 // Each system's arithmetic does not depend on its slot, its neighbours or the
-// tick boundaries (every slice restarts from its own state), so a request's
+// chunk boundaries (every slice restarts from its own state), so a request's
 // results are the same alone and in any mix.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -49,12 +50,13 @@ bool dims(int model, int* n, int* P, int* A, int* E) {
   }
 }
 
+// One-thread-per-system kernel (no work queue) of a model.
 const void* kernel_of(int model, int scheme, int prec) {
   switch (model) {
-    case ODE_DUFFING: return kernel_duffing(scheme, prec, 1);
-    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, 1);
-    case ODE_VALVE: return kernel_valve(scheme, prec, 1);
-    case ODE_BOUNCE: return kernel_bounce(scheme, prec, 1);
+    case ODE_DUFFING: return kernel_duffing(scheme, prec, 0);
+    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, 0);
+    case ODE_VALVE: return kernel_valve(scheme, prec, 0);
+    case ODE_BOUNCE: return kernel_bounce(scheme, prec, 0);
     default: return nullptr;
   }
 }
@@ -70,7 +72,7 @@ struct Request {
   int model = 0;
   int n = 0;
   int periods = 0;
-  int scheduled = 0;  // periods enqueued in ticks so far
+  int scheduled = 0;  // periods enqueued in chunks so far
   int off = -1;       // first slot
   int state = kWaiting;
   bool harvesting = false;
@@ -80,7 +82,11 @@ struct Request {
   double* h_out = nullptr;  // td [2][n], y [n_sys][n], acc [A][n]
   int* h_status = nullptr;
   long long* h_acc_steps = nullptr;
-  cudaEvent_t done_ev = nullptr;
+  cudaEvent_t done_ev = nullptr;   // results copied out
+  cudaEvent_t chunk_ev = nullptr;  // last chunk finished
+  cudaStream_t stream = nullptr;   // borrowed from the server's stream set
+  cudaGraphExec_t graph = nullptr; // one chunk of this request
+  bool chunk_inflight = false;
 };
 
 struct Pool {
@@ -94,17 +100,15 @@ struct Pool {
   double *td = nullptr, *y = nullptr, *p = nullptr, *acc = nullptr;
   int *status = nullptr, *ecnt = nullptr, *left = nullptr;
   long long *nacc = nullptr, *nrej = nullptr;
-  unsigned char* head = nullptr;  // queue head + watchdog flag
-  cudaStream_t stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  cudaEvent_t tick_ev = nullptr;
-  bool tick_inflight = false;
+  unsigned char* head = nullptr;  // watchdog flag
   std::map<int, int> free_ranges;  // offset -> length
   std::deque<Request*> waiting;
   std::vector<Request*> running;
   size_t bytes = 0;
-  long long ticks = 0;
+  long long chunks = 0;
 };
+
+constexpr int kStreams = 32;
 
 }  // namespace
 
@@ -114,6 +118,8 @@ struct ode_server {
   long long budget = 0;
   long long used = 0;
   Pool pools[4];
+  cudaStream_t streams[kStreams] = {};
+  int next_stream = 0;
   std::map<long long, Request*> reqs;
   long long next_ticket = 1;
   std::string err;
@@ -170,49 +176,49 @@ void give_range(Pool& pl, int off, int len) {
   }
 }
 
-// Build the tick graph of a pool: reset the work queue, run slice_periods
-// slices of every occupied slot.
-int build_graph(ode_server* s, Pool& pl) {
+// Capture one chunk of a request: slice_periods slices (at most the request's
+// remaining ones, via the per-slot counts) of its slot range.
+int build_request_graph(ode_server* s, Pool& pl, Request* r) {
   const void* fn = kernel_of(pl.model, pl.scheme, pl.prec);
+  const size_t off = (size_t)r->off;
   KArgs a;
   memset(&a, 0, sizeof(a));
-  a.N = pl.cap;
-  a.td = pl.td;
-  a.y = pl.y;
-  a.p = pl.p;
-  a.acc = pl.acc;
-  a.status = pl.status;
-  a.ecnt = pl.ecnt;
-  a.nacc = pl.nacc;
-  a.nrej = pl.nrej;
+  a.N = r->n;
+  a.ld = pl.cap;
+  a.td = pl.td + off;
+  a.y = pl.y + off;
+  a.p = pl.p + off;
+  a.acc = pl.acc + off;
+  a.status = pl.status + off;
+  a.ecnt = pl.ecnt + off;
+  a.nacc = pl.nacc + off;
+  a.nrej = pl.nrej + off;
   a.records = nullptr;
   a.n_slices = s->slice_periods;
   a.n_skip = s->slice_periods;
   a.h0 = pl.h0;
-  a.slices_left = pl.left;
-  a.queue_head = (unsigned int*)pl.head;
+  a.slices_left = pl.left + off;
+  a.queue_head = nullptr;
   a.flags = (int*)(pl.head + 64);
   a.time_limit_ns = (long long)(pl.time_limit_s * 1e9);
   a.pr = pl.pr;
-  int sms = 0, bps = 0;
-  const int block = 128;
-  SCK(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-  SCK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, 0));
-  if (bps < 1) return sfail(s, ODE_ERR_UNSUPPORTED, "kernel cannot be resident");
-  long long grid = (long long)bps * sms;
-  const long long need = (pl.cap + block - 1) / block;
-  if (grid > need) grid = need;
+  const int block = 64;  // one thread per system, no work queue
+  const unsigned grid = (unsigned)((r->n + block - 1) / block);
   cudaGraph_t g = nullptr;
-  SCK(s, cudaStreamBeginCapture(pl.stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(pl.head, 0, sizeof(unsigned int), pl.stream);
+  SCK(s, cudaGraphCreate(&g, 0));
   void* args[] = {&a};
-  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, 0, pl.stream);
-  cudaError_t e2 = cudaStreamEndCapture(pl.stream, &g);
-  if (e != cudaSuccess) return scuda(s, e, "tick capture");
-  if (e2 != cudaSuccess) return scuda(s, e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&pl.graph, g, 0);
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  kp.func = (void*)fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&r->graph, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return scuda(s, e, "cudaGraphInstantiate");
+  if (e != cudaSuccess) return scuda(s, e, "chunk graph");
   return ODE_OK;
 }
 
@@ -222,45 +228,60 @@ void free_request(Request* r) {
   if (r->h_status) cudaFreeHost(r->h_status);
   if (r->h_acc_steps) cudaFreeHost(r->h_acc_steps);
   if (r->done_ev) cudaEventDestroy(r->done_ev);
+  if (r->chunk_ev) cudaEventDestroy(r->chunk_ev);
+  if (r->graph) cudaGraphExecDestroy(r->graph);
   delete r;
 }
 
 // Copy a request's inputs into its slot range and arm its slice count.
+int launch_chunk(ode_server* s, Pool& pl, Request* r) {
+  SCK(s, cudaGraphLaunch(r->graph, r->stream));
+  SCK(s, cudaEventRecord(r->chunk_ev, r->stream));
+  r->chunk_inflight = true;
+  r->scheduled += s->slice_periods;
+  pl.chunks++;
+  return ODE_OK;
+}
+
 int admit(ode_server* s, Pool& pl, Request* r) {
   const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
   const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
   const double* in = r->h_in;
-  SCK(s, cudaMemcpy2DAsync(pl.td + r->off, pitch, in, row, row, 2, cudaMemcpyHostToDevice, pl.stream));
-  SCK(s, cudaMemcpy2DAsync(pl.y + r->off, pitch, in + 2 * n, row, row, pl.n, cudaMemcpyHostToDevice,
-                           pl.stream));
+  r->stream = s->streams[s->next_stream];
+  s->next_stream = (s->next_stream + 1) % kStreams;
+  cudaStream_t st = r->stream;
+  SCK(s, cudaMemcpy2DAsync(pl.td + r->off, pitch, in, row, row, 2, cudaMemcpyHostToDevice, st));
+  SCK(s, cudaMemcpy2DAsync(pl.y + r->off, pitch, in + 2 * n, row, row, pl.n, cudaMemcpyHostToDevice, st));
   SCK(s, cudaMemcpy2DAsync(pl.p + r->off, pitch, in + (2 + pl.n) * n, row, row, pl.P,
-                           cudaMemcpyHostToDevice, pl.stream));
-  SCK(s, cudaMemsetAsync(pl.nacc + r->off, 0, n * sizeof(long long), pl.stream));
-  SCK(s, cudaMemsetAsync(pl.nrej + r->off, 0, n * sizeof(long long), pl.stream));
-  fill_int_kernel<<<(r->n + 255) / 256 < 1024 ? (r->n + 255) / 256 : 1024, 256, 0, pl.stream>>>(
+                           cudaMemcpyHostToDevice, st));
+  SCK(s, cudaMemsetAsync(pl.nacc + r->off, 0, n * sizeof(long long), st));
+  SCK(s, cudaMemsetAsync(pl.nrej + r->off, 0, n * sizeof(long long), st));
+  fill_int_kernel<<<(r->n + 255) / 256 < 1024 ? (r->n + 255) / 256 : 1024, 256, 0, st>>>(
       pl.left + r->off, r->n, r->periods);
   SCK(s, cudaGetLastError());
+  if (int rc = build_request_graph(s, pl, r)) return rc;
   r->state = kRunning;
   r->scheduled = 0;
   pl.running.push_back(r);
-  return ODE_OK;
+  return launch_chunk(s, pl, r);
 }
 
-// Copy a finished request's results out (after the tick, in stream order).
+// Copy a finished request's results out (after its last chunk, in stream order).
 int harvest(ode_server* s, Pool& pl, Request* r) {
   const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
   const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
   double* out = r->h_out;
-  SCK(s, cudaMemcpy2DAsync(out, row, pl.td + r->off, pitch, row, 2, cudaMemcpyDeviceToHost, pl.stream));
+  cudaStream_t stream = r->stream;
+  SCK(s, cudaMemcpy2DAsync(out, row, pl.td + r->off, pitch, row, 2, cudaMemcpyDeviceToHost, stream));
   SCK(s, cudaMemcpy2DAsync(out + 2 * n, row, pl.y + r->off, pitch, row, pl.n, cudaMemcpyDeviceToHost,
-                           pl.stream));
+                           stream));
   SCK(s, cudaMemcpy2DAsync(out + (2 + pl.n) * n, row, pl.acc + r->off, pitch, row, pl.A,
-                           cudaMemcpyDeviceToHost, pl.stream));
+                           cudaMemcpyDeviceToHost, stream));
   SCK(s, cudaMemcpyAsync(r->h_status, pl.status + r->off, n * sizeof(int), cudaMemcpyDeviceToHost,
-                         pl.stream));
+                         stream));
   SCK(s, cudaMemcpyAsync(r->h_acc_steps, pl.nacc + r->off, n * sizeof(long long),
-                         cudaMemcpyDeviceToHost, pl.stream));
-  SCK(s, cudaEventRecord(r->done_ev, pl.stream));
+                         cudaMemcpyDeviceToHost, stream));
+  SCK(s, cudaEventRecord(r->done_ev, stream));
   r->harvesting = true;
   give_range(pl, r->off, r->n);
   return ODE_OK;
@@ -281,6 +302,16 @@ int ode_server_create(ode_server** out, int device, long long hbm_budget_bytes, 
   s->device = device;
   s->budget = hbm_budget_bytes;
   s->slice_periods = slice_periods;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete s;
+    return ODE_ERR_CUDA;
+  }
+  for (int i = 0; i < kStreams; i++) {
+    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      ode_server_destroy(s);
+      return ODE_ERR_CUDA;
+    }
+  }
   *out = s;
   return ODE_OK;
 }
@@ -349,17 +380,11 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
     SCK(s, cudaMalloc(x.p, x.b));
     SCK(s, cudaMemset(*x.p, 0, x.b));
   }
-  SCK(s, cudaStreamCreateWithFlags(&pl.stream, cudaStreamNonBlocking));
-  SCK(s, cudaEventCreateWithFlags(&pl.tick_ev, cudaEventDisableTiming));
   pl.free_ranges.clear();
   pl.free_ranges[0] = capacity;
   pl.bytes = bytes;
   s->used += (long long)bytes;
   pl.on = true;
-  if (int rc = build_graph(s, pl)) {
-    pl.on = false;
-    return rc;
-  }
   return ODE_OK;
 }
 
@@ -385,6 +410,7 @@ int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, co
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_status, n * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_acc_steps, n * sizeof(long long));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->chunk_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_request(r);
     return scuda(s, e, "request buffers");
@@ -406,24 +432,26 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
   int running = 0, waiting = 0;
   for (Pool& pl : s->pools) {
     if (!pl.on) continue;
-    // 1. a completed tick: account the periods it ran, copy out finished requests
-    if (pl.tick_inflight) {
-      cudaError_t q = cudaEventQuery(pl.tick_ev);
-      if (q == cudaSuccess) {
-        pl.tick_inflight = false;
-        std::vector<Request*> still;
-        for (Request* r : pl.running) {
-          if (r->scheduled >= r->periods) {
-            if (int rc = harvest(s, pl, r)) return rc;
-          } else {
-            still.push_back(r);
-          }
+    // 1. requests whose chunk finished: next chunk, or copy out when done
+    std::vector<Request*> still;
+    for (Request* r : pl.running) {
+      if (r->chunk_inflight) {
+        cudaError_t q = cudaEventQuery(r->chunk_ev);
+        if (q == cudaErrorNotReady) {
+          still.push_back(r);
+          continue;
         }
-        pl.running.swap(still);
-      } else if (q != cudaErrorNotReady) {
-        return scuda(s, q, "tick");
+        if (q != cudaSuccess) return scuda(s, q, "chunk");
+        r->chunk_inflight = false;
+      }
+      if (r->scheduled >= r->periods) {
+        if (int rc = harvest(s, pl, r)) return rc;
+      } else {
+        if (int rc = launch_chunk(s, pl, r)) return rc;
+        still.push_back(r);
       }
     }
+    pl.running.swap(still);
     // 2. admit waiting requests in arrival order while slots are free
     while (!pl.waiting.empty()) {
       Request* r = pl.waiting.front();
@@ -433,18 +461,10 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
       pl.waiting.pop_front();
       if (int rc = admit(s, pl, r)) return rc;
     }
-    // 3. next tick
-    if (!pl.tick_inflight && !pl.running.empty()) {
-      for (Request* r : pl.running) r->scheduled += s->slice_periods;
-      SCK(s, cudaGraphLaunch(pl.graph, pl.stream));
-      SCK(s, cudaEventRecord(pl.tick_ev, pl.stream));
-      pl.tick_inflight = true;
-      pl.ticks++;
-    }
     running += (int)pl.running.size();
     waiting += (int)pl.waiting.size();
   }
-  // 4. requests whose results have arrived
+  // 3. requests whose results have arrived
   for (auto& kv : s->reqs) {
     Request* r = kv.second;
     if (r->harvesting && r->state != kDone) {
@@ -493,18 +513,16 @@ int ode_server_result(ode_server* s, long long ticket, double* td, double* y, do
 int ode_server_destroy(ode_server* s) {
   if (!s) return ODE_OK;
   cudaSetDevice(s->device);
-  for (Pool& pl : s->pools) {
-    if (pl.stream) cudaStreamSynchronize(pl.stream);
-  }
+  for (int i = 0; i < kStreams; i++)
+    if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);
   for (auto& kv : s->reqs) free_request(kv.second);
   for (Pool& pl : s->pools) {
     void* ptrs[] = {pl.td, pl.y, pl.p, pl.acc, pl.status, pl.ecnt, pl.left, pl.nacc, pl.nrej, pl.head};
     for (void* p : ptrs)
       if (p) cudaFree(p);
-    if (pl.graph) cudaGraphExecDestroy(pl.graph);
-    if (pl.tick_ev) cudaEventDestroy(pl.tick_ev);
-    if (pl.stream) cudaStreamDestroy(pl.stream);
   }
+  for (int i = 0; i < kStreams; i++)
+    if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
   delete s;
   return ODE_OK;
 }
