@@ -20,6 +20,7 @@
 //    properties come from the kernel parameter block.
 #pragma once
 
+#include "bits.cuh"
 #include "common.cuh"
 #include "models.cuh"
 
@@ -223,8 +224,8 @@ __device__ __forceinline__ double rpow_fifth(double x) {
 // rule of Sec. 6.6).
 __device__ __forceinline__ bool crossed(const Props& pr, int j, double F_old, double F_new) {
   const double tol = pr.evt_tol[j];
-  const bool down = (F_old > 0.0) && (F_new <= tol);
-  const bool up = (F_old < 0.0) && (F_new >= -tol);
+  const bool down = dpos(F_old) && dle(F_new, tol);
+  const bool up = dneg(F_old) && dle(-tol, F_new);
   const int dir = pr.evt_dir[j];
   return dir < 0 ? down : (dir > 0 ? up : (down || up));
 }
@@ -315,7 +316,7 @@ struct Lane {
       M::events(t, y, p, F);
 #pragma unroll
       for (int j = 0; j < E; j++) {
-        leaving[j] = fabs(F[j]) <= pr.evt_tol[j];
+        leaving[j] = dabs_le(F[j], pr.evt_tol[j]);
         inzone[j] = 0;
         ecnt[j] = 0;
       }
@@ -393,7 +394,7 @@ struct Lane {
       M::events(t, y, p, F);
 #pragma unroll
       for (int j = 0; j < E; j++) {
-        const bool in_zone = fabs(F[j]) <= pr.evt_tol[j];
+        const bool in_zone = dabs_le(F[j], pr.evt_tol[j]);
         if (det[j]) {
           leaving[j] = true;
           inzone[j] = 0;
@@ -488,7 +489,7 @@ struct Lane {
 #pragma unroll
       for (int j = 1; j < E; j++)
         if (j == js) { fold = F[j]; tolj = pr.evt_tol[j]; }
-      if (fabs(fj) <= tolj) {
+      if (dabs_le(fj, tolj)) {
         hi = hs;
 #pragma unroll
         for (int m = 0; m < n; m++) yhi[m] = ynew[m];
@@ -507,14 +508,15 @@ struct Lane {
     if constexpr (SCHEME == kRKCK45) {
       // error ratio and step-size control (Sec. 3, Sec. 6.5)
       // max_m |err_m| / sc_m with a single division: every ratio is brought
-      // over the common denominator prod_m sc_m
+      // over the common denominator prod_m sc_m.  Comparisons, maxima and
+      // finiteness tests run on the integer pipe (all operands >= 0).
       double sc[n], num[n];
 #pragma unroll
-      for (int m = 0; m < n; m++) sc[m] = pr.atol[m] + pr.rtol[m] * fmax(fabs(y[m]), fabs(ynew[m]));
+      for (int m = 0; m < n; m++) sc[m] = fma(pr.rtol[m], dmax_nn(dabs(y[m]), dabs(ynew[m])), pr.atol[m]);
       double den = 1.0;
 #pragma unroll
       for (int m = 0; m < n; m++) {
-        num[m] = fabs(err[m]);
+        num[m] = dabs(err[m]);
 #pragma unroll
         for (int k = 0; k < n; k++)
           if (k != m) num[m] *= sc[k];
@@ -522,10 +524,11 @@ struct Lane {
       }
       double nmax = num[0];
 #pragma unroll
-      for (int m = 1; m < n; m++) nmax = fmax(nmax, num[m]);
+      for (int m = 1; m < n; m++) nmax = dmax_nn(nmax, num[m]);  // NaN propagates
       double errr = nmax / den;
-      if (!(den > 0.0) || !isfinite(den) || !isfinite(nmax)) {
-        // out of range for the common denominator: one division per ratio
+      if (!dpos(den) || !dfinite(den) || !dfinite(nmax)) {
+        // out of range for the common denominator (or NaN): one division
+        // per ratio, NaN kept
         errr = 0.0;
 #pragma unroll
         for (int m = 0; m < n; m++) {
@@ -533,35 +536,35 @@ struct Lane {
           errr = (r > errr || isnan(r)) ? r : errr;
         }
       }
-      bool finite = isfinite(errr);
+      bool finite = dfinite(errr);
 #pragma unroll
-      for (int m = 0; m < n; m++) finite = finite && isfinite(ynew[m]) && !isnan(num[m]);
-      const bool at_min = hs <= pr.hmin;
+      for (int m = 0; m < n; m++) finite = finite && dfinite(ynew[m]);
+      const bool at_min = dbits(hs) <= dbits(pr.hmin);
       if (!finite) {
         nrej++;
         if (at_min) status = kStHminNaN;
-        else h = fmax(pr.shrink * hs, pr.hmin);
+        else h = dmax_nn(pr.shrink * hs, pr.hmin);
         return;
       }
       // new step factor 0.9 err^(-1/5), clamped to [shrink, grow]
       double fac;
-      if (errr <= pr.err_grow) {
+      if (dbits(errr) <= dbits(pr.err_grow)) {
         fac = pr.grow;
-      } else if (errr >= pr.err_shrink) {
+      } else if (dbits(errr) >= dbits(pr.err_shrink)) {
         fac = pr.shrink;
       } else {
-        fac = fmin(fmax(0.9 * rpow_fifth(errr), pr.shrink), pr.grow);
+        fac = dclamp_nn(0.9 * rpow_fifth(errr), pr.shrink, pr.grow);
       }
-      if (errr > 1.0 && !at_min) {
+      if (dbits(errr) > dbits(1.0) && !at_min) {
         nrej++;
-        h = fmin(fmax(hs * fac, pr.hmin), pr.hmax);
+        h = dclamp_nn(hs * fac, pr.hmin, pr.hmax);
         return;
       }
-      hnext = fmin(fmax(hs * fac, pr.hmin), pr.hmax);
+      hnext = dclamp_nn(hs * fac, pr.hmin, pr.hmax);
     } else {
       bool finite = true;
 #pragma unroll
-      for (int m = 0; m < n; m++) finite = finite && isfinite(ynew[m]);
+      for (int m = 0; m < n; m++) finite = finite && dfinite(ynew[m]);
       if (!finite) {
         nrej++;
         status = kStHminNaN;
@@ -588,7 +591,7 @@ struct Lane {
 #pragma unroll
         for (int j = 1; j < E; j++)
           if (j == js) { fj = Fn[j]; tolj = pr.evt_tol[j]; }
-        if (fabs(fj) > tolj) {
+        if (!dabs_le(fj, tolj)) {
           // configuration a of Sec. 4: the step jumped over the zone --
           // locate by bisection in the step size from (t, y)
           locating = true;

@@ -10,6 +10,7 @@
 
 #include <math_constants.h>
 
+#include "bits.cuh"
 #include "common.cuh"
 
 namespace odegpu {
@@ -55,7 +56,7 @@ __device__ __forceinline__ double polytropic_pow(double x, double rx, double e) 
   // binary64): the exponent is then taken as that integer over 5
   const double k5 = 5.0 * e;
   if (fabs(k5 - rint(k5)) <= 1e-12 * k5 && k5 >= 0.0 && k5 <= 60.0 && x > 1e-30 && x < 1e30) {
-    const int k = (int)k5, q = k / 5, r = k % 5;
+    const int k = (int)rint(k5), q = k / 5, r = k % 5;
     double v = 1.0;
     for (int i = 0; i < q; i++) v *= rx;
     if (r) {
@@ -72,8 +73,9 @@ __device__ __forceinline__ double polytropic_pow(double x, double rx, double e) 
 // Ordinary accessories shared by all models (Sec. 6.7): running maximum and
 // minimum of y1 over accepted points, with their times.
 __device__ __forceinline__ void acc_minmax(double t, double y1, double* a) {
-  if (y1 > a[0]) { a[0] = y1; a[1] = t; }
-  if (y1 < a[2]) { a[2] = y1; a[3] = t; }
+  // compared on the integer pipe (finite values; bits.cuh)
+  if (dgt(y1, a[0])) { a[0] = y1; a[1] = t; }
+  if (dlt(y1, a[2])) { a[2] = y1; a[3] = t; }
 }
 
 // --------------------------------------------------------------------------
