@@ -219,6 +219,25 @@ __device__ __forceinline__ double rpow_fifth(double x) {
   return fma(0.2 * z, r, z);
 }
 
+// Root in (0, 1) of the cubic Hermite interpolant of F over one step from its
+// end values F0, F1 (opposite signs) and end slopes D0, D1 (dF/dt times the
+// step): three Newton steps from the secant root, kept inside [0, 1].
+__device__ __forceinline__ double hermite_root(double F0, double F1, double D0, double D1) {
+  double s = F0 / (F0 - F1);
+#pragma unroll
+  for (int it = 0; it < 3; it++) {
+    const double u = 1.0 - s;
+    const double h00 = (1.0 + 2.0 * s) * u * u, h10 = s * u * u;
+    const double h01 = s * s * (3.0 - 2.0 * s), h11 = s * s * (s - 1.0);
+    const double H = h00 * F0 + h10 * D0 + h01 * F1 + h11 * D1;
+    const double dH = (6.0 * s * s - 6.0 * s) * (F0 - F1) + (3.0 * s * s - 4.0 * s + 1.0) * D0 +
+                      (3.0 * s * s - 2.0 * s) * D1;
+    if (dH != 0.0) s -= H / dH;
+    s = fmin(fmax(s, 0.0), 1.0);
+  }
+  return s;
+}
+
 // Is event j crossed in its allowed direction between F_old (outside the
 // zone) and F_new?  Landing inside the zone counts (Sec. 4, MATLAB direction
 // rule of Sec. 6.6).
@@ -260,6 +279,8 @@ struct Lane {
   int ecnt[E];
   T k1[n];
   double lo, hi, yhi[n];
+  double theta_a, theta_b;  // narrowed bracket to verify first
+  int loc_phase;            // 0: try theta_a, 1: try theta_b, 2: bisect
   double fC, fS;    // cos, sin of omega t at the lane's t (binary64 forcing)
   double fCn, fSn;  // the same at t + hs of the last normal trial step
   double w;         // forcing angular frequency
@@ -437,12 +458,19 @@ struct Lane {
     double hs;
     bool last = false;
     if (locating) {
-      const double mid = 0.5 * (lo + hi);
-      if (!(mid > lo && mid < hi) || loc_it >= 200) {
+      double th = 0.5 * (lo + hi);
+      if (loc_phase == 0) th = theta_a;
+      else if (loc_phase == 1) th = theta_b;
+      if (!(th > lo && th < hi)) {
+        // a verification point outside the current bracket: bisect
+        loc_phase = 2;
+        th = 0.5 * (lo + hi);
+      }
+      if (!(th > lo && th < hi) || loc_it >= 200) {
         finish_location(pr);
         return;
       }
-      hs = mid;
+      hs = th;
     } else {
       if (steps >= pr.max_steps) {
         status = kStStepBudget;
@@ -494,13 +522,18 @@ struct Lane {
 #pragma unroll
         for (int m = 0; m < n; m++) yhi[m] = ynew[m];
         finish_location(pr);
-      } else if ((fj > 0.0) == (fold > 0.0)) {
+        return;
+      }
+      const bool pre = dpos(fj) == dpos(fold);
+      if (pre) {
         lo = hs;
       } else {
         hi = hs;
 #pragma unroll
         for (int m = 0; m < n; m++) yhi[m] = ynew[m];
       }
+      // after theta_a: verify theta_b only if the root lies to its right
+      loc_phase = (loc_phase == 0 && pre) ? 1 : 2;
       return;
     }
 
@@ -593,7 +626,12 @@ struct Lane {
           if (j == js) { fj = Fn[j]; tolj = pr.evt_tol[j]; }
         if (!dabs_le(fj, tolj)) {
           // configuration a of Sec. 4: the step jumped over the zone --
-          // locate by bisection in the step size from (t, y)
+          // locate by bisection in the step size from (t, y).  The bracket
+          // [0, hs] is first narrowed to theta* +- 1e-6 hs around the root
+          // of the cubic Hermite interpolant of F (end values and slopes;
+          // one extra right-hand side at the step's end), verified by two
+          // trial steps; bisection then runs inside whatever bracket the
+          // verification leaves.
           locating = true;
           jstar = js;
           loc_it = 0;
@@ -601,6 +639,28 @@ struct Lane {
           hi = hs;
 #pragma unroll
           for (int m = 0; m < n; m++) yhi[m] = ynew[m];
+          double fold = F[0];
+#pragma unroll
+          for (int j = 1; j < E; j++)
+            if (j == js) fold = F[j];
+          T yb[n], f1[n];
+#pragma unroll
+          for (int m = 0; m < n; m++) yb[m] = (T)ynew[m];
+          Stage<T> s1;
+          if constexpr (St::kRotate) {
+            s1.t = t + hs;
+            s1.c = Cn;
+            s1.s = Sn;
+          } else {
+            s1 = St::template stage_at<1, 1>(t, hs, (T)t, (T)hs, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
+          }
+          M::template rhs<T>(s1, yb, pt, mct, f1);
+          const double theta = hs * hermite_root(fold, fj, hs * M::event_rate(js, k1),
+                                                 hs * M::event_rate(js, f1));
+          const double delta = 1e-6 * hs;
+          theta_a = theta - delta;
+          theta_b = theta + delta;
+          loc_phase = (theta == theta) ? 0 : 2;  // NaN: plain bisection
           return;
         }
       }

@@ -104,6 +104,9 @@ struct Duffing {
     F[0] = y[1];
   }
   static __device__ __forceinline__ void action(int, double (&)[N], const double (&)[P]) {}
+  // dF_j/dt from the right-hand side f (F0 = y2)
+  template <class T>
+  static __device__ __forceinline__ double event_rate(int, const T (&f)[N]) { return (double)f[1]; }
   static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
     a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = y[0]; a[5] = t; a[6] = 0.0;
   }
@@ -153,6 +156,8 @@ struct KellerMiksis {
     F[0] = y[1];
   }
   static __device__ __forceinline__ void action(int, double (&)[N], const double (&)[P]) {}
+  template <class T>
+  static __device__ __forceinline__ double event_rate(int, const T (&f)[N]) { return (double)f[1]; }
   static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
     a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t;
   }
@@ -191,6 +196,11 @@ struct Valve {
   static __device__ __forceinline__ void action(int j, double (&y)[N], const double (&p)[P]) {
     if (j == 1) y[1] = -p[4] * y[1];
   }
+  // F0 = y2, F1 = y1
+  template <class T>
+  static __device__ __forceinline__ double event_rate(int j, const T (&f)[N]) {
+    return j == 0 ? (double)f[1] : (double)f[0];
+  }
   static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
     a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = 0.0;
   }
@@ -228,6 +238,9 @@ struct Bounce {
   static __device__ __forceinline__ void action(int j, double (&y)[N], const double (&p)[P]) {
     if (j == 0) y[1] = -p[1] * y[1];
   }
+  // F0 = y1
+  template <class T>
+  static __device__ __forceinline__ double event_rate(int, const T (&f)[N]) { return (double)f[0]; }
   static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
     a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = t; a[5] = y[1];
   }
