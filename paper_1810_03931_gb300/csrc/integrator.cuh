@@ -452,6 +452,31 @@ struct Lane {
     accept(pr, tnew, yhi, false, true);
   }
 
+  // theta* for the narrowed bracket: root of the cubic Hermite interpolant of
+  // event js over the step (t, t + hs) from F and dF/dt at both ends; dF/dt
+  // at the end needs one right-hand side at (t + hs, ynew).  Called once per
+  // located event and kept out of line so that its registers do not raise
+  // the step loop's register count.
+  static __device__ __noinline__ double predict_root(int js, double t, double hs, double f_old,
+                                                     double f_new, double rate_old,
+                                                     const double (&ynew)[n], const T (&pt)[P],
+                                                     const T (&mct)[3], double Cn, double Sn) {
+    T yb[n], f1[n];
+#pragma unroll
+    for (int m = 0; m < n; m++) yb[m] = (T)ynew[m];
+    Stage<T> s1;
+    if constexpr (St::kRotate) {
+      s1.t = t + hs;
+      s1.c = Cn;
+      s1.s = Sn;
+    } else {
+      (void)Cn; (void)Sn;
+      s1 = St::template stage_at<1, 1>(t, hs, (T)t, (T)hs, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
+    }
+    M::template rhs<T>(s1, yb, pt, mct, f1);
+    return hs * hermite_root(f_old, f_new, hs * rate_old, hs * M::event_rate(js, f1));
+  }
+
   // One trial step (normal or bisection).
   __device__ __forceinline__ void trial(const KArgs& a) {
     const Props& pr = a.pr;
@@ -643,20 +668,8 @@ struct Lane {
 #pragma unroll
           for (int j = 1; j < E; j++)
             if (j == js) fold = F[j];
-          T yb[n], f1[n];
-#pragma unroll
-          for (int m = 0; m < n; m++) yb[m] = (T)ynew[m];
-          Stage<T> s1;
-          if constexpr (St::kRotate) {
-            s1.t = t + hs;
-            s1.c = Cn;
-            s1.s = Sn;
-          } else {
-            s1 = St::template stage_at<1, 1>(t, hs, (T)t, (T)hs, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
-          }
-          M::template rhs<T>(s1, yb, pt, mct, f1);
-          const double theta = hs * hermite_root(fold, fj, hs * M::event_rate(js, k1),
-                                                 hs * M::event_rate(js, f1));
+          const double theta =
+              predict_root(js, t, hs, fold, fj, M::event_rate(js, k1), ynew, pt, mct, Cn, Sn);
           const double delta = 1e-6 * hs;
           theta_a = theta - delta;
           theta_b = theta + delta;
@@ -675,18 +688,22 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Launch bounds of the integrator kernels (build-time tunables: fewer
-// registers per thread let more systems be resident at once).
+// Launch bounds of the integrator kernels: at most ODEGPU_MAX_THREADS per
+// block and at least M::kMinBlocks resident blocks of that size per SM (which
+// caps the registers per thread; more resident warps keep the FP64 pipe fed).
+// Both can be overridden at build time (ODEGPU_MIN_BLOCKS for all models).
 #ifndef ODEGPU_MAX_THREADS
 #define ODEGPU_MAX_THREADS 256
 #endif
-#ifndef ODEGPU_MIN_BLOCKS
-#define ODEGPU_MIN_BLOCKS 1
+#ifdef ODEGPU_MIN_BLOCKS
+#define ODEGPU_MIN_BLOCKS_OF(M) ODEGPU_MIN_BLOCKS
+#else
+#define ODEGPU_MIN_BLOCKS_OF(M) M::kMinBlocks
 #endif
 
 // ---- the kernel --------------------------------------------------------------
 template <class M, int SCHEME, int PREC, bool PERSIST>
-__global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS) ode_kernel(const KArgs a) {
+__global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) ode_kernel(const KArgs a) {
   using L_t = Lane<M, SCHEME, PREC>;
   using T = typename L_t::T;
   L_t L;

@@ -88,6 +88,7 @@ __device__ __forceinline__ void acc_minmax(double t, double y1, double* a) {
 struct Duffing {
   static constexpr int N = 2, P = 2, A = 7, E = 1;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
   static constexpr int kForcing = kCosForcing;  // cos(omega t), omega = mc[2]
 
   template <class T>
@@ -131,6 +132,7 @@ struct Duffing {
 struct KellerMiksis {
   static constexpr int N = 2, P = 13, A = 4, E = 1;
   static constexpr bool kHasFP32 = false;
+  static constexpr int kMinBlocks = 1;  // launch bound (registers per thread)
   static constexpr int kForcing = kSinCosForcing;  // sin, cos of 2 pi tau
 
   template <class T>
@@ -177,6 +179,7 @@ struct KellerMiksis {
 struct Valve {
   static constexpr int N = 3, P = 5, A = 5, E = 2;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
   static constexpr int kForcing = kNoForcing;
 
   template <class T>
@@ -221,6 +224,7 @@ struct Valve {
 struct Bounce {
   static constexpr int N = 2, P = 2, A = 6, E = 1;
   static constexpr bool kHasFP32 = true;
+  static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
   static constexpr int kForcing = kNoForcing;
 
   template <class T>
