@@ -62,10 +62,11 @@ enum ode_model { ODE_DUFFING = 0, ODE_KELLER_MIKSIS = 1, ODE_VALVE = 2, ODE_BOUN
 enum ode_scheme { ODE_RK4 = 0, ODE_RKCK45 = 1 };
 
 /* Precision: ODE_FP64 evaluates everything in binary64.  ODE_FP32_RHS
- * evaluates the right-hand-side stages (stage states and f) in binary32 and
- * keeps the state, time, the state update, the embedded error estimate and
- * norm, the step-size controller and event location in binary64.  Available
- * for ODE_DUFFING, ODE_VALVE and ODE_BOUNCE (not for Keller-Miksis). */
+ * evaluates the right-hand-side stages in binary32 (stage states, f, and the
+ * weighted stage sums of the update and of the embedded error estimate) and
+ * keeps the state, time, the state update y + h * sum, the error estimate's
+ * scaling and norm, the step-size controller and event location in binary64.
+ * Available for ODE_DUFFING, ODE_VALVE and ODE_BOUNCE (not Keller-Miksis). */
 enum ode_prec { ODE_FP64 = 0, ODE_FP32_RHS = 1 };
 
 /* CopyModePossibilities of Sec. 6.3, as bit flags. */

@@ -161,12 +161,13 @@ struct Stepper {
       M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k6);
 #pragma unroll
       for (int m = 0; m < n; m++) {
-        // binary64 state update and error estimate
+        // binary64 state update and error estimate; with binary32 stages the
+        // weighted stage sums are formed in binary32 (the stages carry that
+        // rounding already) and promoted once
         const T sb = (T)b1 * k1[m] + (T)b3 * k3[m] + (T)b4 * k4[m] + (T)b6 * k6[m];
         ynew[m] = y[m] + hs * (double)sb;
-        const double se = e1 * (double)k1[m] + e3 * (double)k3[m] + e4 * (double)k4[m] +
-                          e5 * (double)k5[m] + e6 * (double)k6[m];
-        err[m] = hs * se;
+        const T se = (T)e1 * k1[m] + (T)e3 * k3[m] + (T)e4 * k4[m] + (T)e5 * k5[m] + (T)e6 * k6[m];
+        err[m] = hs * (double)se;
       }
     } else {
       T k2[n], k3[n], k4[n];
