@@ -223,6 +223,59 @@ def test_valve_equilibrium_stop_high_flow_rate():
     np.testing.assert_allclose(y1 * np.sqrt(y1 + d), q, rtol=1e-4)
 
 
+def test_valve_full_size_sampled():
+    """The valve sweep at full size (2^16 systems, 1024 + 64 iterations, both
+    events, impacts, equilibrium stops) in the autotuned launch form; sampled
+    systems (corners included) replayed by the oracle one by one."""
+    w = W.valve()
+    s = gpu_solver(w)
+    try:
+        gpu_load(s, w)
+        bs, pers, _ = G.ode_autotune(s, w["h0"], 2)
+        n_rec = w["n_record"]
+        rec = np.zeros((n_rec, 9, w["N"]))
+        G.ode_run_periods(s, w["h0"], w["n_transient"], n_rec, rec)
+        G.ode_synchronize(s)
+        g = gpu_results(s, w, rec)
+    finally:
+        G.ode_destroy(s)
+    idx = W.sample_indices(w["N"], 24, corners=(0, w["N"] // 2, w["N"] - 1))
+    ws = W.subset(w, idx)
+    o = run_oracle(ws, NTHREADS)
+    o2 = run_oracle(ws, NTHREADS, rtol=1e-10, atol=1e-10)
+    gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    tol = 100 * w["evt_tol"][0]
+    stable = _valve_stable(ws, o, o2, tol)
+    assert stable.sum() >= 16
+    _valve_compare(gs, o, stable, tol)
+    # the high-flow-rate end of the sweep rests at the equilibrium (Sec. 7.3)
+    assert np.all(g["status"][w["p"][3] > 9.0] == G.ODE_ST_EQUILIBRIUM)
+
+
+def test_keller_miksis_bench_size_sampled():
+    """The Keller-Miksis sweep of the bench (2^18 systems, 16 + 16 acoustic
+    periods) in the autotuned launch form; sampled systems replayed by the
+    oracle (C0..C12 computed independently on each side)."""
+    w = W.keller_miksis(n_transient=16, n_record=16)
+    s = gpu_solver(w)
+    try:
+        gpu_load(s, w)
+        G.ode_autotune(s, w["h0"], 1)
+        rec = np.zeros((16, 7, w["N"]))
+        G.ode_run_periods(s, w["h0"], 16, 16, rec)
+        G.ode_synchronize(s)
+        g = gpu_results(s, w, rec)
+    finally:
+        G.ode_destroy(s)
+    assert np.all(g["status"] == 1)
+    idx = W.sample_indices(w["N"], 24, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    ws = W.subset(w, idx)
+    mask, o = _nonchaotic(ws, 16, 16, cont_rows=(4, 5), rtol=1e-10, agree=1e-8)
+    gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    assert mask.sum() >= 12
+    _compare_records(gs, o, mask, 4, 2, tol=1e-8, exact_rows=(6,))
+
+
 # ---------------------------------------------------------------------------
 # Bouncing ball: impact law against its closed form on the GPU too.
 # ---------------------------------------------------------------------------
