@@ -332,7 +332,7 @@ def run_gpu(args):
             "launch": tune if tune else {"block": args.block, "persistent": args.persistent},
             "clocks": clk,
         }
-        if not args.no_cpu_baseline and world == 1 or (world > 1 and not args.no_cpu_baseline):
+        if not args.no_cpu_baseline and world == 1:  # CPU baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -244,8 +244,10 @@ const char *ode_last_error(const ode_solver *s);
 /* ---- helpers ------------------------------------------------------------- */
 
 /* Keller-Miksis coefficients C0..C12, Eqs. (16)-(28), from physical
- * parameters in SI units (omega in rad/s); C must hold 13 doubles.  C8 is
- * computed as printed (with omega_1).  Pure host computation. */
+ * parameters in SI units (omega in rad/s); C must hold 13 doubles.  C8 uses
+ * omega_2 (Eq. (24) prints omega_1, but the derivative of P_A2 sin(omega_2 t)
+ * gives omega_2; only omega_2 agrees with the dimensional equation).  Pure
+ * host computation. */
 int ode_km_coefficients(double PA1, double PA2, double omega1, double omega2, double theta,
                         double RE, double Pinf, double pV, double sigma, double mu, double rho,
                         double cL, double gamma, double *C);

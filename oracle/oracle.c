@@ -695,8 +695,10 @@ int orc_rhs(const orc_config *c, double t, const double *y, const double *p,
 
 /* ------------------------------------------------------------------------ */
 /* Keller-Miksis coefficients C0..C12, Eqs. (16)-(28), from the physical     */
-/* parameters of Sec. 2.2 (SI units; omega in rad/s).  C8 is written as      */
-/* printed in Eq. (24), with omega_1.                                        */
+/* parameters of Sec. 2.2 (SI units; omega in rad/s).  Eq. (24) prints C8    */
+/* with omega_1; the time derivative of P_A2 sin(omega_2 t) in Eq. (8) gives */
+/* omega_2, which is what is used (an independent integration of the         */
+/* dimensional Eqs. (8)-(11) with two frequencies agrees only with omega_2). */
 /* ------------------------------------------------------------------------ */
 void orc_km_coefficients(double PA1, double PA2, double omega1, double omega2,
                          double theta, double RE, double Pinf, double pV,
@@ -715,7 +717,7 @@ void orc_km_coefficients(double PA1, double PA2, double omega1, double omega2,
     C[5] = PA1 / rho * s2;
     C[6] = PA2 / rho * s2;
     C[7] = RE * omega1 * PA1 / (rho * cL) * s2;
-    C[8] = RE * omega1 * PA2 / (rho * cL) * s2;
+    C[8] = RE * omega2 * PA2 / (rho * cL) * s2;
     C[9] = RE * omega1 / (two_pi * cL);
     C[10] = 3.0 * gamma;
     C[11] = omega2 / omega1;

@@ -784,7 +784,7 @@ int ode_km_coefficients(double PA1, double PA2, double omega1, double omega2, do
   C[5] = PA1 * L2 / rho;
   C[6] = PA2 * L2 / rho;
   C[7] = RE * omega1 * PA1 * L2 / (rho * cL);
-  C[8] = RE * omega1 * PA2 * L2 / (rho * cL);
+  C[8] = RE * omega2 * PA2 * L2 / (rho * cL);  // omega_2: d/dt of P_A2 sin(omega_2 t)
   C[9] = RE * omega1 / (2.0 * M_PI * cL);
   C[10] = 3.0 * gamma;
   C[11] = omega2 / omega1;

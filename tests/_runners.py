@@ -15,11 +15,19 @@ from paper_1810_03931_gb300 import odegpu as G
 DIMS = {0: (2, 2, 7, 1), 1: (2, 13, 4, 1), 2: (3, 5, 5, 2), 3: (2, 2, 6, 1)}  # n, P, A, E
 
 
+def _second(w):
+    N = w["N"]
+    pa2 = w.get("PA2", np.zeros(N))
+    om2 = w.get("omega2", w["omega"])
+    return pa2, om2
+
+
 def km_params_gpu(w):
     ph = w["phys"]
+    pa2, om2 = _second(w)
     P = np.zeros((13, w["N"]))
     for i in range(w["N"]):
-        P[:, i] = G.ode_km_coefficients(w["PA"][i], 0.0, w["omega"][i], w["omega"][i], 0.0, ph["RE"],
+        P[:, i] = G.ode_km_coefficients(w["PA"][i], pa2[i], w["omega"][i], om2[i], 0.0, ph["RE"],
                                         ph["Pinf"], ph["pV"], ph["sigma"], ph["mu"], ph["rho"], ph["cL"],
                                         ph["gamma"])
     return P
@@ -27,7 +35,8 @@ def km_params_gpu(w):
 
 def km_params_oracle(w):
     ph = w["phys"]
-    return O.km_coefficients(w["PA"], w["omega"], PA2=0.0, omega2=w["omega"], theta=0.0, **ph)
+    pa2, om2 = _second(w)
+    return O.km_coefficients(w["PA"], w["omega"], PA2=pa2, omega2=om2, theta=0.0, **ph)
 
 
 def gpu_solver(w, prec=G.ODE_FP64, persistent=0, block=0, device=0):

@@ -30,6 +30,8 @@ MUTANTS = [
      [P.test_km_zero_amplitude_rests_at_equilibrium]),
     ("km_denominator", "double den = y1 - C[9] * y1 * y2 + C[4] * C[9];", "double den = y1 - C[9] * y1 * y2;",
      [lambda: P.test_km_dimensionless_matches_dimensional(1.2e5, 300e3)]),
+    ("km_c8_printed_omega1", "C[8] = RE * omega2 * PA2 / (rho * cL) * s2;",
+     "C[8] = RE * omega1 * PA2 / (rho * cL) * s2;", [P.test_km_dual_frequency_matches_dimensional]),
     ("valve_sqrt", "q - y[0] * sqrt(y[2])", "q - y[0] * y[2]",
      [P.test_valve_high_flow_rate_settles_to_equilibrium]),
     ("accessory_min", "if (y[0] < a[2]) { a[2] = y[0]; a[3] = t; }", "if (y[0] > a[2]) { a[2] = y[0]; a[3] = t; }",

@@ -447,23 +447,26 @@ def test_km_zero_amplitude_rests_at_equilibrium():
     assert f_plus < 0 < f_minus
 
 
-def _km_dimensional(PA, f, T_periods):
+def _km_dimensional(PA, f, T_periods, PA2=0.0, f2=None):
     """Independent integration of the dimensional Keller-Miksis equation,
-    Eqs. (8)-(11), for R(t) in SI units (scipy DOP853)."""
+    Eqs. (8)-(11), for R(t) in SI units (scipy DOP853), with one or two
+    excitation frequencies (theta = 0)."""
     from scipy.integrate import solve_ivp
     ph = O.KM_WATER
     rho, c, sig, mu, pV, Pinf, gam, RE = (ph[k] for k in ("rho", "cL", "sigma", "mu", "pV", "Pinf",
                                                           "gamma", "RE"))
     w = 2 * math.pi * f
+    w2 = 2 * math.pi * (f if f2 is None else f2)
     Pg0 = Pinf - pV + 2 * sig / RE
 
     def rhs(t, u):
         R, Rd = u
         pG = Pg0 * (RE / R) ** (3 * gam)
         pL = pG + pV - 2 * sig / R - 4 * mu * Rd / R
-        pinf = Pinf + PA * math.sin(w * t)
+        pinf = Pinf + PA * math.sin(w * t) + PA2 * math.sin(w2 * t)
         # d/dt (p_L - p_inf) without its R'' part, which is moved to the left
-        dp = -3 * gam * pG * Rd / R + 2 * sig * Rd / R ** 2 + 4 * mu * Rd ** 2 / R ** 2 - PA * w * math.cos(w * t)
+        dp = (-3 * gam * pG * Rd / R + 2 * sig * Rd / R ** 2 + 4 * mu * Rd ** 2 / R ** 2
+              - PA * w * math.cos(w * t) - PA2 * w2 * math.cos(w2 * t))
         lhs = (1 - Rd / c) * R + 4 * mu / (rho * c)
         rhs_ = (1 + Rd / c) * (pL - pinf) / rho + R / (rho * c) * dp - (1 - Rd / (3 * c)) * 1.5 * Rd ** 2
         return [Rd, rhs_ / lhs]
@@ -481,6 +484,19 @@ def test_km_dimensionless_matches_dimensional(PA, f):
     y1_ref, y2_ref = _km_dimensional(PA, f, 3)
     np.testing.assert_allclose(r["records"][:, 4, 0], y1_ref, rtol=1e-8)
     np.testing.assert_allclose(r["records"][:, 5, 0], y2_ref, rtol=1e-6, atol=1e-8)
+
+
+def test_km_dual_frequency_matches_dimensional():
+    """Two excitation frequencies (Eq. (9)): the dimensionless Eqs. (12)-(28)
+    against the dimensional Eqs. (8)-(11).  This pins C8 to omega_2 (the
+    printed omega_1 is off by 0.4 % here)."""
+    PA1, PA2, f1, f2 = 0.5e5, 0.7e5, 100e3, 170e3
+    C = O.km_coefficients([PA1], [2 * math.pi * f1], PA2=PA2, omega2=2 * math.pi * f2, theta=0.0)
+    assert C[11, 0] == f2 / f1
+    cfg = O.make_config(O.KELLER_MIKSIS, O.RKCK45, 1e-3, rtol=1e-12, atol=1e-12, td_mode=O.TD_SHIFT)
+    r = O.run(cfg, [[0.0], [1.0]], [[1.0], [0.0]], C, n_slices=3, record=True)
+    y1_ref, _ = _km_dimensional(PA1, f1, 3, PA2=PA2, f2=f2)
+    np.testing.assert_allclose(r["records"][:, 4, 0], y1_ref, rtol=1e-8)
 
 
 # --------------------------------------------------------------------------

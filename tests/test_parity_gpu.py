@@ -154,6 +154,25 @@ def test_keller_miksis_parity():
     assert np.all(np.abs(g["records"][:, 4, pa0] - 1.0) < 1e-8)
 
 
+@pytest.mark.parametrize("make", [lambda: W.keller_miksis_collapse(6, 6, 6, 4),
+                                  lambda: W.keller_miksis_dual(3, 3, 4, 3)],
+                         ids=["collapse_iteration", "dual_frequency"])
+def test_keller_miksis_collapse_protocols(make):
+    """Collapse-to-collapse iteration (event stop at each maximum, t0 moved to
+    the stop time, t1 = 1e6), single and dual frequency (Sec. 7.2).  The
+    located maxima are fixed to the event tolerance 1e-6, so the acceptance is
+    100 x that tolerance on well-conditioned points."""
+    w = make()
+    tol = 100 * w["evt_tol"][0]
+    mask, o = _nonchaotic(w, w["n_transient"], w["n_record"], cont_rows=(4, 5, 6), rtol=1e-10, agree=tol)
+    g = run_gpu(w)
+    assert np.all(g["status"] == G.ODE_ST_EVENT_STOP)
+    assert mask.sum() >= w["N"] // 3
+    # each record is one collapse: it starts at a maximum, so y2 ~ 0 at both ends
+    assert np.all(np.abs(g["records"][:, 5]) <= w["evt_tol"][0])
+    _compare_records(g, o, mask, 4, 2, tol=tol)
+
+
 # ---------------------------------------------------------------------------
 # Pressure relief valve with two events, impact action and equilibrium stop
 # (Sec. 7.3), per-sweep and persistent launches.

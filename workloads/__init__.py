@@ -81,6 +81,39 @@ def keller_miksis(npa=512, nf=512, n_transient=1024, n_record=64, pa_max=2.0e5):
                  phys=dict(KM_PHYS), n_transient=n_transient, n_record=n_record)
 
 
+def keller_miksis_collapse(npa=8, nf=8, n_transient=16, n_record=8, pa_max=2.0e5):
+    """The collapse-to-collapse iteration of Sec. 7.2: each slice runs from a
+    local maximum of the radius to the next (event y2 = 0 downwards, stop 1,
+    tolerance 1e-6), t1 = 1e6 and the Finalization moving t0 to the stop time,
+    so a record holds (tau_max, y1_max, tau_min, y1_min) of one collapse.
+    Single frequency on the pA x f grid of the benchmark sweep without its
+    unforced row (an unforced bubble has no maximum to stop at)."""
+    w = keller_miksis(npa + 1, nf, n_transient, n_record, pa_max)
+    keep = w["PA"] > 0
+    N = int(keep.sum())
+    w.update(N=N, PA=w["PA"][keep], omega=w["omega"][keep], y0=np.ascontiguousarray(w["y0"][:, keep]))
+    w.update(name="keller_miksis_collapse_%dx%d" % (npa, nf), td=np.vstack([np.zeros(N), np.full(N, 1e6)]),
+             events_on=True, evt_dir=(-1,), evt_tol=(1e-6,), evt_stop=(1,), td_mode=TD_T0_TO_T)
+    return w
+
+
+def keller_miksis_dual(nf1=4, nf2=4, n_transient=8, n_record=4):
+    """The four-dimensional dual-frequency scan of Sec. 7.2 (Table 5): P_A1 in
+    {0.5, 1.1} bar, P_A2 in {0.7, 1.2} bar, f1 and f2 log-spaced in
+    [20, 1000] kHz (f2 fastest), theta = 0, iterated collapse to collapse."""
+    pa1 = np.array([0.5e5, 1.1e5])
+    pa2 = np.array([0.7e5, 1.2e5])
+    f = np.logspace(math.log10(20e3), math.log10(1000e3), max(nf1, nf2))
+    f1, f2 = f[:nf1], f[:nf2]
+    A1, A2, F1, F2 = (x.ravel() for x in np.meshgrid(pa1, pa2, f1, f2, indexing="ij"))
+    N = A1.size
+    return _base(name="keller_miksis_dual_%d" % N, model=KELLER_MIKSIS, scheme=RKCK45, N=N, h0=1e-2,
+                 td=np.vstack([np.zeros(N), np.full(N, 1e6)]), y0=np.vstack([np.ones(N), np.zeros(N)]),
+                 PA=A1, omega=2 * math.pi * F1, PA2=A2, omega2=2 * math.pi * F2, phys=dict(KM_PHYS),
+                 events_on=True, evt_dir=(-1,), evt_tol=(1e-6,), evt_stop=(1,), td_mode=TD_T0_TO_T,
+                 n_transient=n_transient, n_record=n_record)
+
+
 def valve(N=65536, n_transient=1024, n_record=64, rtol=1e-9):
     q = np.linspace(0.2, 10.0, N)
     v = VALVE_FIXED
@@ -111,7 +144,7 @@ def subset(w, idx):
     for key in ("td", "y0", "p"):
         if key in w:
             out[key] = np.ascontiguousarray(w[key][:, idx])
-    for key in ("PA", "omega"):
+    for key in ("PA", "omega", "PA2", "omega2"):
         if key in w:
             out[key] = np.ascontiguousarray(w[key][idx])
     out["name"] = w["name"] + "_sub%d" % len(idx)
