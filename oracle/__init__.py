@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-DUFFING, KELLER_MIKSIS, VALVE, BOUNCE = 0, 1, 2, 3
+DUFFING, KELLER_MIKSIS, VALVE, BOUNCE, DUFFING_LYAPUNOV = 0, 1, 2, 3, 4
 RK4, RKCK45 = 0, 1
 TD_KEEP, TD_T0_TO_T, TD_SHIFT = 0, 1, 2
 ST_NONE, ST_TEND, ST_EVENT_STOP, ST_EQUILIBRIUM, ST_HMIN_NAN, ST_STEP_BUDGET = range(6)
@@ -173,6 +173,7 @@ def dims(model: int):
 
 DEFAULT_MC = {
     DUFFING: (-1.0, 1.0, 1.0),   # delta, c3, omega: x'' + k x' + x + x^3 = B cos t
+    DUFFING_LYAPUNOV: (-1.0, 1.0, 1.0),
 }
 
 

@@ -9,7 +9,9 @@
  * handling state machine (Sec. 4, Sec. 6.6), accessories (Sec. 5, Sec. 6.7),
  * initialization / finalization hooks (Sec. 6.8) and the three test models of
  * Sec. 2 (Duffing Eqs. (1)-(2), Keller-Miksis Eqs. (12)-(28), pressure relief
- * valve Eqs. (29)-(34)), plus a bouncing ball used only for closed-form pins.
+ * valve Eqs. (29)-(34)), the Duffing equation extended by its linearisation
+ * in polar coordinates for the largest Lyapunov exponent (Eqs. (3)-(7)), plus
+ * a bouncing ball used only for closed-form pins.
  *
  * Only tests/, the smoke check and the benchmark's CPU-baseline leg may load
  * this file's library. It shares no code with the CUDA library and neither
@@ -54,7 +56,8 @@
 #define ORC_MAXA 8
 #define ORC_MAXE 2
 
-enum { ORC_DUFFING = 0, ORC_KELLER_MIKSIS = 1, ORC_VALVE = 2, ORC_BOUNCE = 3 };
+enum { ORC_DUFFING = 0, ORC_KELLER_MIKSIS = 1, ORC_VALVE = 2, ORC_BOUNCE = 3,
+       ORC_DUFFING_LYAPUNOV = 4 };
 enum { ORC_RK4 = 0, ORC_RKCK45 = 1 };
 enum { ORC_TD_KEEP = 0, ORC_TD_T0_TO_T = 1, ORC_TD_SHIFT = 2 };
 enum {
@@ -108,6 +111,7 @@ int orc_dims(int model, int *n, int *P, int *A, int *E)
     case ORC_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return 0;
     case ORC_VALVE:         *n = 3; *P = 5;  *A = 5; *E = 2; return 0;
     case ORC_BOUNCE:        *n = 2; *P = 2;  *A = 6; *E = 1; return 0;
+    case ORC_DUFFING_LYAPUNOV: *n = 4; *P = 2; *A = 5; *E = 1; return 0;
     default: return -1;
     }
 }
@@ -125,6 +129,25 @@ static void rhs_duffing(const orc_config *c, double t, const double *y,
     double k = p[0], B = p[1];
     f[0] = y[1];
     f[1] = delta * y[0] - c3 * y[0] * y[0] * y[0] - k * y[1] + B * cos(w * t);
+}
+
+/* Duffing with its linearisation attached in polar coordinates, Eqs. (3)-(6):
+ * y3 is the radius and y4 the angle of a tangent vector of (y1, y2),
+ *   y3' = y3 ((1 + g1) sin(y4) cos(y4) + g2 sin(y4)^2),
+ *   y4' = -sin(y4)^2 + (g1 cos(y4) + g2 sin(y4)) cos(y4),
+ * with g1 = dF2/dy1 = delta - 3 c3 y1^2 and g2 = dF2/dy2 = -k, F2 the
+ * right-hand side of y2.  Same p and mc as the Duffing model. */
+static void rhs_duffing_lyapunov(const orc_config *c, double t, const double *y,
+                                 const double *p, double *f)
+{
+    double delta = c->mc[0], c3 = c->mc[1];
+    double k = p[0];
+    rhs_duffing(c, t, y, p, f);
+    double g1 = delta - 3.0 * c3 * y[0] * y[0];
+    double g2 = -k;
+    double s = sin(y[3]), co = cos(y[3]);
+    f[2] = y[2] * ((1.0 + g1) * s * co + g2 * s * s);
+    f[3] = -s * s + (g1 * co + g2 * s) * co;
 }
 
 /* Keller-Miksis in the dimensionless form of Eqs. (12)-(15); p = C0..C12 of
@@ -174,6 +197,7 @@ static void rhs(const orc_config *c, double t, const double *y,
     case ORC_DUFFING:       rhs_duffing(c, t, y, p, f); break;
     case ORC_KELLER_MIKSIS: rhs_keller_miksis(t, y, p, f); break;
     case ORC_VALVE:         rhs_valve(y, p, f); break;
+    case ORC_DUFFING_LYAPUNOV: rhs_duffing_lyapunov(c, t, y, p, f); break;
     default:                rhs_bounce(y, p, f); break;
     }
 }
@@ -189,6 +213,7 @@ static void event_functions(const orc_config *c, double t, const double *y,
     case ORC_DUFFING:       F[0] = y[1]; break;             /* extrema of y1 */
     case ORC_KELLER_MIKSIS: F[0] = y[1]; break;
     case ORC_VALVE:         F[0] = y[1]; F[1] = y[0]; break; /* max, impact */
+    case ORC_DUFFING_LYAPUNOV: F[0] = y[1]; break;
     default:                F[0] = y[0]; break;             /* ball on floor */
     }
 }
@@ -209,6 +234,7 @@ static void event_action(const orc_config *c, int j, double *y, const double *p)
 /*              a6 = number of detections of event 0                          */
 /*  valve:      a4 = number of impacts (event 1)                             */
 /*  ball:       a4 = time of the last impact, a5 = velocity before it        */
+/*  Lyapunov:   a4 = ln y3 at the end of the slice (Finalization, below)      */
 /* ------------------------------------------------------------------------ */
 static void acc_initialization(const orc_config *c, double t, const double *y,
                                double *a)
@@ -218,6 +244,7 @@ static void acc_initialization(const orc_config *c, double t, const double *y,
     case ORC_DUFFING: a[4] = y[0]; a[5] = t; a[6] = 0.0; break;
     case ORC_VALVE:   a[4] = 0.0; break;
     case ORC_BOUNCE:  a[4] = t; a[5] = y[1]; break;
+    case ORC_DUFFING_LYAPUNOV: a[4] = 0.0; break;
     default: break;
     }
 }
@@ -564,6 +591,14 @@ static int integrate_slice(const orc_config *c, int n, int A, int E,
         double span = t1 - t0;
         td[0] = t;
         td[1] = t + span;
+    }
+    /* Lyapunov model: the stretch of the tangent vector over the slice is
+     * kept as ln y3 and the radius restarts from one (Sec. 2.1, Eq. (7):
+     * y3 is reset at every Poincare point t_n; the exponent is the mean of
+     * ln y3(t_n) per unit time -- the printed Eq. (7) averages y3 itself). */
+    if (c->model == ORC_DUFFING_LYAPUNOV) {
+        a[4] = log(y[2]);
+        y[2] = 1.0;
     }
     return status;
 }

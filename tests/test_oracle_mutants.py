@@ -38,6 +38,15 @@ MUTANTS = [
      [P.test_accessories_equal_brute_force_over_accepted_points]),
     ("zone_at_start", "leaving[j] = fabs(F[j]) <= c->evt_tol[j];", "leaving[j] = 0;",
      [P.test_event_inside_zone_at_start_is_not_detected]),
+    ("lyap_one_plus_g1", "f[2] = y[2] * ((1.0 + g1) * s * co + g2 * s * s);",
+     "f[2] = y[2] * (g1 * s * co + g2 * s * s);",
+     [P.test_lyapunov_linear_oscillator_matches_matrix_exponential]),
+    ("lyap_angle_sign", "f[3] = -s * s + (g1 * co + g2 * s) * co;", "f[3] = s * s + (g1 * co + g2 * s) * co;",
+     [P.test_lyapunov_linear_oscillator_matches_matrix_exponential]),
+    ("lyap_g1_cubic_factor", "double g1 = delta - 3.0 * c3 * y[0] * y[0];", "double g1 = delta - c3 * y[0] * y[0];",
+     [lambda: P.test_lyapunov_nonlinear_against_cartesian_tangent_flow(-1.0)]),
+    ("lyap_radius_not_reset", "        y[2] = 1.0;\n", "",
+     [P.test_lyapunov_linear_oscillator_matches_matrix_exponential]),
 ]
 
 

@@ -271,6 +271,85 @@ def test_duffing_event_times_against_scipy(k):
     np.testing.assert_allclose(tr["ev_y"][:, 0], s.y_events[0][:, 0], rtol=0, atol=1e-9)
 
 
+# --------------------------------------------------------------------------
+# Lyapunov model, Eqs. (3)-(7): the polar linearisation (radius y3, angle y4)
+# against the tangent flow written in Cartesian coordinates, u' = v,
+# v' = g1 u + g2 v, with the radius reset at every slice end.
+# --------------------------------------------------------------------------
+def _lyap_oracle(mc, k, B, y0, n_per, rtol=1e-12):
+    cfg = O.make_config(O.DUFFING_LYAPUNOV, O.RKCK45, 1e-2, rtol=rtol, atol=rtol, mc=mc,
+                        td_mode=O.TD_SHIFT)
+    N = len(k)
+    td = np.vstack([np.zeros(N), np.full(N, 2 * math.pi)])
+    r = O.run(cfg, td, np.asarray(y0, dtype=float), np.vstack([k, B]), n_slices=n_per, record=True)
+    assert np.all(r["status"] == O.ST_TEND)
+    return r["records"]  # (slice, A + n + 1, N), A = 5: a4 = ln y3 of the slice
+
+
+def test_lyapunov_linear_oscillator_matches_matrix_exponential():
+    # delta = -1, c3 = 0: constant tangent matrix J = [[0, 1], [-1, -k]], so
+    # over slice s the tangent vector is expm(J T) applied s times to
+    # (cos phi0, sin phi0); the slice's ln-stretch and end direction follow.
+    from scipy.linalg import expm
+    k = np.array([0.05, 0.2, 0.7, 1.3])
+    phi0 = np.array([0.3, -1.0, 2.0, 4.0])
+    N, n_per, T = len(k), 4, 2 * math.pi
+    y0 = np.vstack([np.full(N, -0.5), np.full(N, 0.1), np.ones(N), phi0])
+    rec = _lyap_oracle((-1.0, 0.0, 1.0), k, np.full(N, 0.3), y0, n_per)
+    for i in range(N):
+        M = expm(np.array([[0.0, 1.0], [-1.0, -k[i]]]) * T)
+        e = np.array([math.cos(phi0[i]), math.sin(phi0[i])])
+        for s_ in range(n_per):
+            e_new = M @ e
+            stretch = math.log(np.linalg.norm(e_new) / np.linalg.norm(e))
+            e = e_new
+            assert abs(rec[s_, 4, i] - stretch) < 1e-9
+            assert rec[s_, 5 + 2, i] == 1.0  # radius reset to one
+            d = e / np.linalg.norm(e)
+            assert abs(math.cos(rec[s_, 5 + 3, i]) - d[0]) < 1e-9
+            assert abs(math.sin(rec[s_, 5 + 3, i]) - d[1]) < 1e-9
+
+
+def test_lyapunov_linear_oscillator_exponent_is_minus_half_damping():
+    # the largest exponent of x'' + k x' + x = B cos t is -k / 2 (k < 2); the
+    # mean of ln y3 per unit time over n periods differs from it by a
+    # bounded term / (n T)
+    k = np.array([0.1, 0.4, 1.0])
+    N, n_per, T = len(k), 200, 2 * math.pi
+    y0 = np.vstack([np.full(N, -0.5), np.full(N, 0.1), np.ones(N), np.zeros(N)])
+    rec = _lyap_oracle((-1.0, 0.0, 1.0), k, np.full(N, 0.3), y0, n_per, rtol=1e-10)
+    lam = rec[:, 4, :].sum(axis=0) / (n_per * T)
+    np.testing.assert_allclose(lam, -k / 2, rtol=0, atol=2e-3)
+
+
+@pytest.mark.parametrize("delta", [-1.0, 1.0])
+def test_lyapunov_nonlinear_against_cartesian_tangent_flow(delta):
+    from scipy.integrate import solve_ivp
+    k, B, n_per, T = 0.25, 0.3, 3, 2 * math.pi
+    phi0 = 0.7
+
+    def f(t, z):
+        y1, y2, u, v = z
+        g1 = delta - 3.0 * y1 * y1
+        return [y2, delta * y1 - y1 ** 3 - k * y2 + B * math.cos(t), v, g1 * u - k * v]
+
+    z0 = [-0.5, 0.1, math.cos(phi0), math.sin(phi0)]
+    sol = solve_ivp(f, (0, n_per * T), z0, method="DOP853", rtol=1e-13, atol=1e-14,
+                    t_eval=[T * (s_ + 1) for s_ in range(n_per)])
+    rec = _lyap_oracle((delta, 1.0, 1.0), np.array([k]), np.array([B]),
+                       np.array([[-0.5], [0.1], [1.0], [phi0]]), n_per)
+    norm_prev = 1.0
+    for s_ in range(n_per):
+        y1, y2, u, v = sol.y[:, s_]
+        nrm = math.hypot(u, v)
+        # ln of the slice's stretch: the reset makes the stretches telescope
+        assert abs(rec[s_, 4, 0] - math.log(nrm / norm_prev)) < 1e-8
+        norm_prev = nrm
+        assert abs(rec[s_, 5 + 0, 0] - y1) < 1e-9 and abs(rec[s_, 5 + 1, 0] - y2) < 1e-9
+        assert abs(math.cos(rec[s_, 5 + 3, 0]) - u / nrm) < 1e-8
+        assert abs(math.sin(rec[s_, 5 + 3, 0]) - v / nrm) < 1e-8
+
+
 def test_event_brute_force_tiny():
     """Brute force: sample F on a fine fixed grid of an independent integration
     and bracket every downward crossing; each located time lies in a bracket."""
