@@ -43,11 +43,19 @@ import workloads as W  # noqa: E402
 # (+ 6 sqrt).  Keller-Miksis RKCK45: 6 x 36 + 10 + 70 + 18 + 20 + 10 + 20 + 1
 # = 365 (+ 6 pow, 6 sincospi, 12 div).
 FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365}
+# The binary32 right-hand-side form splits those flops: binary64 keeps the
+# update (1 fma per component), the error estimate (1 mul per component), the
+# error norm, the controller and the time update; the rest (right-hand sides,
+# stage times and states, weighted stage sums) is binary32.  Duffing RKCK45:
+# 4 + 2 + 10 + 20 + 1 = 37 binary64, 209 - 37 = 172 binary32.  Valve:
+# 6 + 3 + 15 + 20 + 1 = 45 binary64, 274 - 45 = 229 binary32.
+FLOPS_FP32RHS = {"duffing_rkck": (37, 172), "valve": (45, 229)}
 # transcendental calls per accepted step, converted to DFMA equivalents with
 # the library's call-cost probe (one DFMA = 2 flops) for the FMA-peak roofline
 TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {},
                    "keller_miksis": {"pow": 6, "cos": 12}}
 METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
+METRIC_FP32RHS = "accepted system-steps/s (binary32 RHS stages, binary64 state and control, rtol 1e-10)"
 UNIT = "system-steps/s"
 
 
@@ -294,10 +302,21 @@ def run_gpu(args):
     dfma, ffma = G.ode_probe_fma_peak(local)
     cos_eq, pow_eq = G.ode_probe_call_cost(local)
     peak_tflops = 2 * 2 * sms * max_mhz * 1e6 / 1e12
+    peak32_tflops = 128 * 2 * sms * max_mhz * 1e6 / 1e12  # 128 binary32 FMA lanes per SM
     arith = FLOPS_PER_STEP.get(args.workload, 0)
     trans = TRANSCENDENTALS.get(args.workload, {})
     eq = {"cos": cos_eq, "pow": pow_eq}
     per_step = arith + sum(2.0 * eq[k] * v for k, v in trans.items())
+    fp32_split = None
+    if args.prec == "fp32rhs":
+        # mixed precision: the fraction of the step time the two FMA pipes
+        # need at their peaks; achieved is stated in binary64-equivalent flops
+        # (binary32 flops x peak64 / peak32); forcing evaluations not counted
+        f64, f32 = FLOPS_FP32RHS.get(args.workload, (arith, 0))
+        arith = f64 + f32 * peak_tflops / peak32_tflops
+        per_step = arith
+        trans = {}
+        fp32_split = {"fp64_flops_per_step": f64, "fp32_flops_per_step": f32, "peak_fp32": peak32_tflops}
     achieved_tflops = per_step * steps_per_pass / (ms_step * 1e-3) / 1e12
     achieved_arith = arith * steps_per_pass / (ms_step * 1e-3) / 1e12
 
@@ -312,7 +331,8 @@ def run_gpu(args):
     if rank == 0:
         value = tot_steps / (max_ms * 1e-3)
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if args.prec == "fp64" else METRIC_FP32RHS, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32 rhs / f64 state",
             "data": "synthetic",
@@ -329,9 +349,14 @@ def run_gpu(args):
                          "transcendentals_per_step": trans,
                          "call_cost_dfma_equiv": {"cos": round(cos_eq, 2), "pow": round(pow_eq, 2)},
                          "achieved_arith_only": achieved_arith, "frac_arith_only": achieved_arith / peak_tflops},
+            # accepted steps differ between forms (the binary32 error estimate
+            # carries rounding noise): system-periods/s compares them on work
+            "system_periods_per_s": world * w["N"] * (w["n_transient"] + w["n_record"]) / (max_ms * 1e-3),
             "launch": tune if tune else {"block": args.block, "persistent": args.persistent},
             "clocks": clk,
         }
+        if fp32_split is not None:
+            line["roofline"].update(fp32_split, unit="TFLOP/s (binary64-equivalent)")
         if not args.no_cpu_baseline and world == 1:  # CPU baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         print(json.dumps(line), flush=True)

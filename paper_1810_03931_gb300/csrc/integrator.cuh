@@ -74,6 +74,42 @@ __device__ __forceinline__ void small_angle_c(double x, double U, double& cd, do
 
 constexpr double kSmallAngle = 0.1;
 
+// (sin, cos)(a) in binary32 for a binary64 angle a: a is reduced to
+// r = a - k pi/2 in [-pi/4, pi/4] in binary64 (k = rint(a 2/pi) by adding
+// 1.5 * 2^52, whose low mantissa bits then hold k mod 4), r is rounded once,
+// and the Taylor series of sin and cos at 0 up to r^9 / 9! and r^10 / 10!
+// (first omitted terms below 2e-10) are evaluated in binary32; the quadrant
+// k mod 4 swaps and negates them.  Valid for |a| < 2^50.
+__device__ __forceinline__ void sincos_quarter(double a, float& s, float& c) {
+  constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
+  const double ks = fma(a, 2.0 / CUDART_PI, kShift);
+  const int q = __double2loint(ks) & 3;
+  const float r = (float)fma(-(ks - kShift), 0.5 * CUDART_PI, a);
+  const float r2 = r * r;
+  const float sr =
+      r * fmaf(fmaf(fmaf(fmaf(r2, (float)sin_coef(1.0, 4), (float)sin_coef(1.0, 3)), r2,
+                          (float)sin_coef(1.0, 2)),
+                     r2, (float)sin_coef(1.0, 1)),
+                r2, 1.0f);
+  const float cr = fmaf(fmaf(fmaf(fmaf(fmaf(r2, (float)cos_coef(1.0, 5), (float)cos_coef(1.0, 4)), r2,
+                                       (float)cos_coef(1.0, 3)),
+                                  r2, (float)cos_coef(1.0, 2)),
+                             r2, (float)cos_coef(1.0, 1)),
+                        r2, 1.0f);
+  const float ns = -sr, nc = -cr;
+  s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? ns : nc;
+  c = (q == 0) ? cr : (q == 1) ? ns : (q == 2) ? nc : sr;
+}
+
+// Binary32 rotation factors for the angle c x, |x| <= 0.1: Taylor series in
+// U = x^2 up to U^2 (first omitted terms below 1.4e-9).
+template <int CNUM, int CDEN>
+__device__ __forceinline__ void small_angle_f(float x, float U, float& cd, float& sd) {
+  constexpr double c = (double)CNUM / (double)CDEN;
+  cd = fmaf(fmaf(U, (float)cos_coef(c, 2), (float)cos_coef(c, 1)), U, 1.0f);
+  sd = x * fmaf(fmaf(U, (float)sin_coef(c, 2), (float)sin_coef(c, 1)), U, (float)sin_coef(c, 0));
+}
+
 // ---- one trial step --------------------------------------------------------
 // From (t, y) with step hs and the cached first stage k1 = f(t, y), compute
 // the new state ynew and (RKCK45) the error estimate err = hs * sum e_i k_i.
@@ -82,6 +118,11 @@ constexpr double kSmallAngle = 0.1;
 // a stage at t + c hs gets (cos, sin)(omega (t + c hs)) by angle addition with
 // d = omega c hs, and the c = 1 stage returns them in (Cn, Sn) as the anchor
 // of the next step.  Large d (long steps) falls back to sincos.
+// Harmonic forcing in binary32: the anchor (C, S) = (cos, sin)(omega t) comes
+// from sincos_quarter (binary64 reduction of omega t, binary32 series) once
+// per accepted step, and a stage rotates it by c omega hs in binary32.
+// Rounding t itself to binary32 would put an error of ulp(t) / 2 into the
+// phase (2.4e-4 rad at t = 7000).
 template <class M, int SCHEME, int PREC>
 struct Stepper {
   static constexpr int n = M::N, P = M::P;
@@ -93,8 +134,8 @@ struct Stepper {
   // addition when |omega hs| <= 0.1 (x = omega hs, U = x^2 precomputed).
   template <int CNUM, int CDEN>
   static __device__ __forceinline__ Stage<T> stage_at(double t, double hs, T tb, T h,
-                                                      const T (&mct)[3], double C, double S,
-                                                      double w, double x, double U, bool small) {
+                                                      const T (&mct)[3], T C, T S, double w,
+                                                      double x, double U, bool small, T xw) {
     constexpr double c = (double)CNUM / (double)CDEN;
     Stage<T> st;
     if constexpr (kRotate) {
@@ -108,11 +149,19 @@ struct Stepper {
         sincos(w * st.t, &st.s, &st.c);
       }
     } else {
-      (void)t; (void)hs; (void)C; (void)S; (void)w; (void)x; (void)U; (void)small;
+      (void)mct; (void)U;
       st.t = tb + (T)c * h;
       if constexpr (M::kForcing != kNoForcing) {
-        sincos_t(M::omega(mct) * st.t, &st.s, &st.c);
+        if (small) {
+          T cd, sd;
+          small_angle_f<CNUM, CDEN>(xw, xw * xw, cd, sd);
+          st.c = C * cd - S * sd;
+          st.s = S * cd + C * sd;
+        } else {
+          sincos_quarter(fma(c, w * hs, w * t), st.s, st.c);
+        }
       } else {
+        (void)t; (void)hs; (void)C; (void)S; (void)w; (void)x; (void)small; (void)xw;
         st.c = st.s = (T)0;
       }
     }
@@ -121,7 +170,7 @@ struct Stepper {
 
   static __device__ __forceinline__ void step(double t, const double (&y)[n], double hs,
                                               const T (&pt)[P], const T (&mct)[3],
-                                              const T (&k1)[n], double C, double S, double w,
+                                              const T (&k1)[n], T C, T S, double w,
                                               double (&ynew)[n], double (&err)[n], double& Cn,
                                               double& Sn) {
     T yb[n];
@@ -131,25 +180,26 @@ struct Stepper {
     const T tb = (T)t;
     const double x = w * hs, U = x * x;
     const bool small = fabs(x) <= kSmallAngle;
+    const T xw = (!kRotate && M::kForcing != kNoForcing) ? (T)x : (T)0;
     T ys[n];
     if constexpr (SCHEME == kRKCK45) {
       using namespace ck;
       T k2[n], k3[n], k4[n], k5[n], k6[n];
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a21 * k1[m]);
-      M::template rhs<T>(stage_at<1, 5>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k2);
+      M::template rhs<T>(stage_at<1, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k2);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a31 * k1[m] + (T)a32 * k2[m]);
-      M::template rhs<T>(stage_at<3, 10>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k3);
+      M::template rhs<T>(stage_at<3, 10>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h, (T)a41 * k1[m] + (T)a42 * k2[m] + (T)a43 * k3[m]);
-      M::template rhs<T>(stage_at<3, 5>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k4);
+      M::template rhs<T>(stage_at<3, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k4);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a51 * k1[m] + (T)a52 * k2[m] + (T)a53 * k3[m] + (T)a54 * k4[m]);
-      const Stage<T> s5 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small);
+      const Stage<T> s5 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
       M::template rhs<T>(s5, ys, pt, mct, k5);
       Cn = (double)s5.c;
       Sn = (double)s5.s;
@@ -158,7 +208,7 @@ struct Stepper {
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a61 * k1[m] + (T)a62 * k2[m] + (T)a63 * k3[m] + (T)a64 * k4[m] +
                           (T)a65 * k5[m]);
-      M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small), ys, pt, mct, k6);
+      M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k6);
 #pragma unroll
       for (int m = 0; m < n; m++) {
         // binary64 state update and error estimate; with binary32 stages the
@@ -172,7 +222,7 @@ struct Stepper {
     } else {
       T k2[n], k3[n], k4[n];
       const T half = (T)0.5;
-      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small);
+      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
       M::template rhs<T>(sh, ys, pt, mct, k2);
@@ -181,7 +231,7 @@ struct Stepper {
       M::template rhs<T>(sh, ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
-      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small);
+      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
       M::template rhs<T>(s4, ys, pt, mct, k4);
       Cn = (double)s4.c;
       Sn = (double)s4.s;
@@ -284,6 +334,7 @@ struct Lane {
   int loc_phase;            // 0: try theta_a, 1: try theta_b, 2: bisect
   double fC, fS;    // cos, sin of omega t at the lane's t (binary64 forcing)
   double fCn, fSn;  // the same at t + hs of the last normal trial step
+  T gC, gS;         // binary32 form: cos, sin of omega t at the lane's t
   double w;         // forcing angular frequency
 
   // Load the slot; false when the system has no slice to run in this launch.
@@ -461,18 +512,23 @@ struct Lane {
   static __device__ __noinline__ double predict_root(int js, double t, double hs, double f_old,
                                                      double f_new, double rate_old,
                                                      const double (&ynew)[n], const T (&pt)[P],
-                                                     const T (&mct)[3], double Cn, double Sn) {
+                                                     const T (&mct)[3], double Cn, double Sn,
+                                                     double w) {
     T yb[n], f1[n];
 #pragma unroll
     for (int m = 0; m < n; m++) yb[m] = (T)ynew[m];
     Stage<T> s1;
     if constexpr (St::kRotate) {
+      (void)w;
       s1.t = t + hs;
       s1.c = Cn;
       s1.s = Sn;
     } else {
       (void)Cn; (void)Sn;
-      s1 = St::template stage_at<1, 1>(t, hs, (T)t, (T)hs, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
+      s1.t = (T)(t + hs);
+      s1.c = s1.s = (T)0;
+      if constexpr (M::kForcing != kNoForcing) sincos_quarter(w * (t + hs), s1.s, s1.c);
+      else (void)w;
     }
     M::template rhs<T>(s1, yb, pt, mct, f1);
     return hs * hermite_root(f_old, f_new, hs * rate_old, hs * M::event_rate(js, f1));
@@ -518,13 +574,19 @@ struct Lane {
         st0.c = fC;
         st0.s = fS;
       } else {
-        st0 = St::template stage_at<0, 1>(t, 0.0, (T)t, (T)0, mct, 0.0, 0.0, 0.0, 0.0, 0.0, true);
+        // binary32 forcing anchor at the new t, kept for the trials from t
+        if constexpr (M::kForcing != kNoForcing) sincos_quarter(w * t, gS, gC);
+        else gC = gS = (T)0;
+        st0.t = (T)t;
+        st0.c = gC;
+        st0.s = gS;
       }
       M::template rhs<T>(st0, yb, pt, mct, k1);
       k1ok = true;
     }
     double ynew[n], err[n], Cn = 0.0, Sn = 0.0;
-    St::step(t, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
+    if constexpr (St::kRotate) St::step(t, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
+    else St::step(t, y, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
     if (!locating) {
       fCn = Cn;
       fSn = Sn;
@@ -670,7 +732,7 @@ struct Lane {
           for (int j = 1; j < E; j++)
             if (j == js) fold = F[j];
           const double theta =
-              predict_root(js, t, hs, fold, fj, M::event_rate(js, k1), ynew, pt, mct, Cn, Sn);
+              predict_root(js, t, hs, fold, fj, M::event_rate(js, k1), ynew, pt, mct, Cn, Sn, w);
           const double delta = 1e-6 * hs;
           theta_a = theta - delta;
           theta_b = theta + delta;

@@ -333,6 +333,24 @@ def test_fp32_rhs_duffing_and_valve_report(tmp_path):
         rows.append((w["name"], float(err), float(g["nacc"].sum() / o["nacc"].sum())))
     for r in rows:
         print("FP32_RHS %s: max |end state - oracle| = %.3e, accepted steps vs oracle = %.3f" % r)
+    # not a tolerance claim: a bound far above binary32 rounding that a wrong
+    # forcing quadrant, sign or phase would exceed
+    assert rows[0][1] < 1e-5
+
+
+def test_fp32_rhs_forcing_phase_at_large_t():
+    # the same Duffing sweep started 1000 forcing periods later: the binary32
+    # forcing keeps the phase to binary32 rounding of a reduced angle, so the
+    # error stays at the level of the run from t = 0 (a phase taken from t
+    # rounded to binary32 would be off by up to 2.4e-4 rad here)
+    w = W.duffing_rkck(16, 8, 4, 2)
+    w = dict(w, td=w["td"] + 2000.0 * np.pi)
+    o = run_oracle(w, NTHREADS)
+    g = run_gpu(w, prec=G.ODE_FP32_RHS)
+    A, n = DIMS[w["model"]][2], DIMS[w["model"]][0]
+    err = np.max(np.abs(g["records"][:, A:A + n] - o["records"][:, A:A + n]))
+    print("FP32_RHS duffing from t = 2000 pi: max |end state - oracle| = %.3e" % err)
+    assert err < 1e-5
 
 
 # ---------------------------------------------------------------------------
