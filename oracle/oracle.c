@@ -595,10 +595,14 @@ static int integrate_slice(const orc_config *c, int n, int A, int E,
     /* Lyapunov model: the stretch of the tangent vector over the slice is
      * kept as ln y3 and the radius restarts from one (Sec. 2.1, Eq. (7):
      * y3 is reset at every Poincare point t_n; the exponent is the mean of
-     * ln y3(t_n) per unit time -- the printed Eq. (7) averages y3 itself). */
+     * ln y3(t_n) per unit time -- the printed Eq. (7) averages y3 itself).
+     * The angle is brought back to [-pi, pi]: Eqs. (3)-(4) see it only
+     * through sin and cos, and an angle that winds without bound would
+     * loosen its relative tolerance (the paper is silent on this). */
     if (c->model == ORC_DUFFING_LYAPUNOV) {
         a[4] = log(y[2]);
         y[2] = 1.0;
+        y[3] = remainder(y[3], 2.0 * M_PI);
     }
     return status;
 }
