@@ -10,7 +10,7 @@ one whole pass: reset the initial conditions from HBM, integrate every system
 over all 1088 periods in one persistent launch, write the 64 records.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       [--workload duffing_rkck|duffing_rk4|valve|keller_miksis]
+       [--workload duffing_rkck|duffing_rk4|valve|keller_miksis|duffing_lyapunov]
 Under torchrun each rank integrates its own sweep (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
@@ -41,8 +41,11 @@ import workloads as W  # noqa: E402
 # Duffing RK4: 4 x 10 + stage times 4 + stage states 14 + update 18 + 1 = 77
 # (+ 4 cos).  Valve RKCK45: 6 x 11 + 10 + 105 + 27 + 30 + 15 + 20 + 1 = 274
 # (+ 6 sqrt).  Keller-Miksis RKCK45: 6 x 36 + 10 + 70 + 18 + 20 + 10 + 20 + 1
-# = 365 (+ 6 pow, 6 sincospi, 12 div).
-FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365}
+# = 365 (+ 6 pow, 6 sincospi, 12 div).  Duffing with its polar
+# linearisation (n = 4): 6 x 23 + 10 + 140 + 36 + 40 + 20 + 20 + 1 = 405
+# (+ 6 cos of the forcing, 6 sincos of the angle, credited as cos).
+FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365,
+                  "duffing_lyapunov": 405}
 # The binary32 right-hand-side form splits those flops: binary64 keeps the
 # update (1 fma per component), the error estimate (1 mul per component), the
 # error norm, the controller and the time update; the rest (right-hand sides,
@@ -53,7 +56,7 @@ FLOPS_FP32RHS = {"duffing_rkck": (37, 172), "valve": (45, 229)}
 # transcendental calls per accepted step, converted to DFMA equivalents with
 # the library's call-cost probe (one DFMA = 2 flops) for the FMA-peak roofline
 TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {},
-                   "keller_miksis": {"pow": 6, "cos": 12}}
+                   "keller_miksis": {"pow": 6, "cos": 12}, "duffing_lyapunov": {"cos": 12}}
 METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
 METRIC_FP32RHS = "accepted system-steps/s (binary32 RHS stages, binary64 state and control, rtol 1e-10)"
 UNIT = "system-steps/s"
@@ -68,6 +71,8 @@ def workload(name, rank=0):
         return W.valve()
     if name == "keller_miksis":
         return W.keller_miksis(n_transient=16, n_record=16)
+    if name == "duffing_lyapunov":
+        return W.duffing_lyapunov()
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -191,6 +196,11 @@ def run_gpu(args):
     from _runners import DIMS, km_params_gpu
 
     w = workload(args.workload, rank)
+    if args.order == "shuffled":
+        # the same systems in a seeded random order: neighbouring lanes no
+        # longer share similar parameters (the "clustering" remark of Sec. 7.2)
+        perm = np.random.default_rng(W.SEED).permutation(w["N"])
+        w = dict(W.subset(w, perm), name=w["name"] + "_shuffled")
     if args.n_transient is not None:
         w["n_transient"] = args.n_transient
     if args.n_record is not None:
@@ -565,7 +575,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="duffing_rkck",
-                    choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "serving"])
+                    choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "duffing_lyapunov",
+                             "serving"])
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per run")
     ap.add_argument("--slice-periods", type=int, default=2, help="serving: periods per tick")
     ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
@@ -581,6 +592,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--order", default="grid", choices=["grid", "shuffled"],
+                    help="system order: parameter grid (neighbours similar) or seeded shuffle")
     ap.add_argument("--n-transient", type=int, default=None, help="override (profiling runs)")
     ap.add_argument("--n-record", type=int, default=None, help="override (profiling runs)")
     args = ap.parse_args()

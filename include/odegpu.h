@@ -49,13 +49,29 @@ typedef struct ode_solver ode_solver; /* opaque; the ParametricODESolver object 
  *                     A=5, E=2 (F0 = y2, F1 = y1 with impact y2 <- -r y2)
  *  ODE_BOUNCE         bouncing ball (closed-form checks): n=2, P=2 (g, r),
  *                     A=6, E=1 (F0 = y1 with impact y2 <- -r y2)
+ *  ODE_DUFFING_LYAPUNOV  Eqs. (1)-(6): the Duffing model with its
+ *                     linearisation in polar coordinates attached (y3 =
+ *                     radius, y4 = angle of a tangent vector): n=4, P=2
+ *                     (k, B), A=5, E=1 (F0 = y2), constants as ODE_DUFFING.
+ *                     Finalization (Sec. 6.8, Eq. (7)) stores a4 = ln y3,
+ *                     resets y3 = 1 and reduces y4 modulo 2 pi to [-pi, pi]
+ *                     at every slice end, so the largest
+ *                     Lyapunov exponent is the mean of a4 over slices divided
+ *                     by the slice length (Eq. (7) as printed averages y3
+ *                     itself; the logarithm is read).  Binary64 only.
  * Accessories (Sec. 5, Sec. 6.7), all models: a0 = max y1, a1 = its time,
  *   a2 = min y1, a3 = its time (over accepted points of one slice);
  *   Duffing a4, a5 = y1 and t at the first detection of event 0, a6 = count
  *   of event-0 detections; valve a4 = number of impacts; ball a4 = time of the
  *   last impact, a5 = velocity just before it.  Initialization (Sec. 6.8)
  *   sets a0..a5 from the state at the slice start and counts to zero. */
-enum ode_model { ODE_DUFFING = 0, ODE_KELLER_MIKSIS = 1, ODE_VALVE = 2, ODE_BOUNCE = 3 };
+enum ode_model {
+  ODE_DUFFING = 0,
+  ODE_KELLER_MIKSIS = 1,
+  ODE_VALVE = 2,
+  ODE_BOUNCE = 3,
+  ODE_DUFFING_LYAPUNOV = 4
+};
 
 /* Schemes (Sec. 3, Sec. 6.4): classic fixed-step RK4 and the adaptive
  * Runge-Kutta-Cash-Karp 4(5) pair (fifth-order solution propagated). */
@@ -142,8 +158,8 @@ int ode_set_tolerances(ode_solver *s, const double *rtol, const double *atol, do
 int ode_set_events(ode_solver *s, int enabled, const int *direction, const double *tolerance,
                    const int *stop_count, int max_steps_in_zone);
 
-/* Solver-wide model constants (host array, nc <= 8 doubles).  Duffing:
- * (delta, c3, omega).  Other models take none (nc = 0). */
+/* Solver-wide model constants (host array, nc <= 8 doubles).  Duffing and
+ * Duffing-Lyapunov: (delta, c3, omega).  Other models take none (nc = 0). */
 int ode_set_model_constants(ode_solver *s, const double *c, int nc);
 
 /* Finalization time-domain update (enum ode_td_mode). */

@@ -78,5 +78,11 @@ const void* kernel_duffing(int scheme, int prec, int persistent);
 const void* kernel_keller_miksis(int scheme, int prec, int persistent);
 const void* kernel_valve(int scheme, int prec, int persistent);
 const void* kernel_bounce(int scheme, int prec, int persistent);
+const void* kernel_duffing_lyapunov(int scheme, int prec, int persistent);
+
+// Model dimensions (n, P, A, E) of the compiled hooks; false for an unknown
+// model.  The kernel of a model for (scheme, precision, launch form), or null.
+bool model_dims(int model, int* n, int* P, int* A, int* E);
+const void* kernel_for(int model, int scheme, int prec, int persistent);
 
 }  // namespace odegpu

@@ -411,7 +411,8 @@ struct Lane {
     anchor_forcing();
   }
 
-  // End of a slice: Finalization time-domain update (Sec. 6.8) and record.
+  // End of a slice: Finalization (Sec. 6.8) -- the time-domain update and the
+  // model's own hook -- and the record.
   __device__ __forceinline__ void end_slice(const KArgs& a) {
     const double t_end = t;
     if (a.pr.td_mode == kTdT0ToT) {
@@ -421,6 +422,7 @@ struct Lane {
       t0 = t_end;
       t1 = t_end + span;
     }
+    M::finalize(y, acc);
     if (a.records != nullptr && slice >= a.n_skip) {
       const int N = a.N;
       constexpr int R = A + n + 1;

@@ -120,7 +120,8 @@ struct Duffing {
       a[6] = (double)cnt;
       if (cnt == 1) { a[4] = y[0]; a[5] = t; }
     }
-  }
+  }  // Finalization hook (Sec. 6.8) on the state and accessories: nothing to do
+  static __device__ __forceinline__ void finalize(double (&)[N], double (&)[A]) {}
 };
 
 // --------------------------------------------------------------------------
@@ -166,7 +167,8 @@ struct KellerMiksis {
   static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
     acc_minmax(t, y[0], a);
   }
-  static __device__ __forceinline__ void acc_event(int, int, double, const double (&)[N], double (&)[A]) {}
+  static __device__ __forceinline__ void acc_event(int, int, double, const double (&)[N], double (&)[A]) {}  // Finalization hook (Sec. 6.8) on the state and accessories: nothing to do
+  static __device__ __forceinline__ void finalize(double (&)[N], double (&)[A]) {}
 };
 
 // --------------------------------------------------------------------------
@@ -213,7 +215,8 @@ struct Valve {
   static __device__ __forceinline__ void acc_event(int j, int cnt, double, const double (&)[N],
                                                    double (&a)[A]) {
     if (j == 1) a[4] = (double)cnt;
-  }
+  }  // Finalization hook (Sec. 6.8) on the state and accessories: nothing to do
+  static __device__ __forceinline__ void finalize(double (&)[N], double (&)[A]) {}
 };
 
 // --------------------------------------------------------------------------
@@ -254,6 +257,66 @@ struct Bounce {
   static __device__ __forceinline__ void acc_event(int j, int, double t, const double (&y)[N],
                                                    double (&a)[A]) {
     if (j == 0) { a[4] = t; a[5] = y[1]; }
+  }  // Finalization hook (Sec. 6.8) on the state and accessories: nothing to do
+  static __device__ __forceinline__ void finalize(double (&)[N], double (&)[A]) {}
+};
+
+
+// --------------------------------------------------------------------------
+// Duffing with its linearisation attached in polar coordinates for the
+// largest Lyapunov exponent, Eqs. (3)-(6): y3 is the radius and y4 the angle
+// of a tangent vector of (y1, y2),
+//   y3' = y3 ((1 + g1) sin y4 cos y4 + g2 sin^2 y4),
+//   y4' = -sin^2 y4 + (g1 cos y4 + g2 sin y4) cos y4,
+// g1 = dF2/dy1 = delta - 3 c3 y1^2, g2 = dF2/dy2 = -k.  p and mc as Duffing.
+// Event 0: F = y2.  Accessories a0..a3 min/max of y1 with times; a4 = ln y3
+// at the slice end, where the Finalization hook restarts the radius from one
+// (Eq. (7): the exponent is the mean of ln y3(t_n) per unit time) and reduces
+// the angle modulo 2 pi.
+// --------------------------------------------------------------------------
+struct DuffingLyapunov {
+  static constexpr int N = 4, P = 2, A = 5, E = 1;
+  static constexpr bool kHasFP32 = false;
+  static constexpr int kMinBlocks = 1;  // launch bound (registers per thread)
+  static constexpr int kForcing = kCosForcing;  // cos(omega t), omega = mc[2]
+
+  template <class T>
+  static __device__ __forceinline__ T omega(const T (&mc)[3]) { return mc[2]; }
+  template <class T>
+  static __device__ __forceinline__ void rhs(const Stage<T>& st, const T (&y)[N], const T (&p)[P],
+                                             const T (&mc)[3], T (&f)[N]) {
+    const T y1s = y[0] * y[0];
+    f[0] = y[1];
+    f[1] = y[0] * (mc[0] - mc[1] * y1s) - p[0] * y[1] + p[1] * st.c;
+    const T g1 = mc[0] - (T)3 * mc[1] * y1s;
+    T s, c;
+    sincos_t(y[3], &s, &c);
+    const T ss = s * s;
+    f[2] = y[2] * (((T)1 + g1) * (s * c) - p[0] * ss);
+    f[3] = (g1 * c - p[0] * s) * c - ss;
+  }
+  static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
+                                                double (&F)[E]) {
+    F[0] = y[1];
+  }
+  static __device__ __forceinline__ void action(int, double (&)[N], const double (&)[P]) {}
+  template <class T>
+  static __device__ __forceinline__ double event_rate(int, const T (&f)[N]) { return (double)f[1]; }
+  static __device__ __forceinline__ void acc_init(double t, const double (&y)[N], double (&a)[A]) {
+    a[0] = y[0]; a[1] = t; a[2] = y[0]; a[3] = t; a[4] = 0.0;
+  }
+  static __device__ __forceinline__ void acc_ordinary(double t, const double (&y)[N], double (&a)[A]) {
+    acc_minmax(t, y[0], a);
+  }
+  static __device__ __forceinline__ void acc_event(int, int, double, const double (&)[N], double (&)[A]) {}
+  // Finalization hook (Sec. 6.8): keep the slice's stretch, restart the
+  // radius, and bring the angle back to [-pi, pi] (the right-hand side sees
+  // it only through sin and cos; an unbounded angle would loosen its
+  // relative tolerance)
+  static __device__ __forceinline__ void finalize(double (&y)[N], double (&a)[A]) {
+    a[4] = log(y[2]);
+    y[2] = 1.0;
+    y[3] = remainder(y[3], 2.0 * CUDART_PI);
   }
 };
 

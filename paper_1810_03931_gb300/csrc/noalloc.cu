@@ -52,26 +52,6 @@ cudaError_t scratch_address(int device, unsigned char** out) {
   return cudaSuccess;
 }
 
-bool dims_of(int model, int* n, int* P, int* A, int* E) {
-  switch (model) {
-    case ODE_DUFFING: *n = 2; *P = 2; *A = 7; *E = 1; return true;
-    case ODE_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return true;
-    case ODE_VALVE: *n = 3; *P = 5; *A = 5; *E = 2; return true;
-    case ODE_BOUNCE: *n = 2; *P = 2; *A = 6; *E = 1; return true;
-    default: return false;
-  }
-}
-
-const void* persistent_kernel(int model, int scheme, int prec) {
-  switch (model) {
-    case ODE_DUFFING: return kernel_duffing(scheme, prec, 1);
-    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, 1);
-    case ODE_VALVE: return kernel_valve(scheme, prec, 1);
-    case ODE_BOUNCE: return kernel_bounce(scheme, prec, 1);
-    default: return nullptr;
-  }
-}
-
 thread_local char g_msg[256];
 
 int bad(const char* m) {
@@ -102,10 +82,10 @@ extern "C" int ode_run_periods_noalloc(const ode_noalloc_settings* cfg, int n_sy
   g_msg[0] = 0;
   if (!cfg) return bad("settings are NULL");
   int n, P, A, E;
-  if (!dims_of(cfg->model, &n, &P, &A, &E)) return bad("unknown model");
+  if (!model_dims(cfg->model, &n, &P, &A, &E)) return bad("unknown model");
   if (cfg->scheme != ODE_RK4 && cfg->scheme != ODE_RKCK45) return bad("unknown scheme");
   if (cfg->prec != ODE_FP64 && cfg->prec != ODE_FP32_RHS) return bad("unknown precision");
-  const void* fn = persistent_kernel(cfg->model, cfg->scheme, cfg->prec);
+  const void* fn = kernel_for(cfg->model, cfg->scheme, cfg->prec, 1);
   if (!fn) return bad("no kernel for this model / scheme / precision");
   if (n_systems < 1) return bad("n_systems must be >= 1");
   if (n_systems > kNoAllocMaxSystems)

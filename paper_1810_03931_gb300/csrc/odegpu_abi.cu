@@ -19,6 +19,30 @@
 
 using namespace odegpu;
 
+namespace odegpu {
+bool model_dims(int model, int* n, int* P, int* A, int* E) {
+  switch (model) {
+    case ODE_DUFFING: *n = 2; *P = 2; *A = 7; *E = 1; return true;
+    case ODE_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return true;
+    case ODE_VALVE: *n = 3; *P = 5; *A = 5; *E = 2; return true;
+    case ODE_BOUNCE: *n = 2; *P = 2; *A = 6; *E = 1; return true;
+    case ODE_DUFFING_LYAPUNOV: *n = 4; *P = 2; *A = 5; *E = 1; return true;
+    default: return false;
+  }
+}
+
+const void* kernel_for(int model, int scheme, int prec, int persistent) {
+  switch (model) {
+    case ODE_DUFFING: return kernel_duffing(scheme, prec, persistent);
+    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, persistent);
+    case ODE_VALVE: return kernel_valve(scheme, prec, persistent);
+    case ODE_BOUNCE: return kernel_bounce(scheme, prec, persistent);
+    case ODE_DUFFING_LYAPUNOV: return kernel_duffing_lyapunov(scheme, prec, persistent);
+    default: return nullptr;
+  }
+}
+}  // namespace odegpu
+
 struct ode_solver {
   int model, scheme, prec, N, device;
   int n, P, A, E;
@@ -63,27 +87,6 @@ int cuda_fail(ode_solver* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
   } while (0)
 
-// Model dimensions (n, P, A, E) of the compiled hooks.
-bool model_dims(int model, int* n, int* P, int* A, int* E) {
-  switch (model) {
-    case ODE_DUFFING: *n = 2; *P = 2; *A = 7; *E = 1; return true;
-    case ODE_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return true;
-    case ODE_VALVE: *n = 3; *P = 5; *A = 5; *E = 2; return true;
-    case ODE_BOUNCE: *n = 2; *P = 2; *A = 6; *E = 1; return true;
-    default: return false;
-  }
-}
-
-const void* kernel_for(int model, int scheme, int prec, int persistent) {
-  switch (model) {
-    case ODE_DUFFING: return kernel_duffing(scheme, prec, persistent);
-    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, persistent);
-    case ODE_VALVE: return kernel_valve(scheme, prec, persistent);
-    case ODE_BOUNCE: return kernel_bounce(scheme, prec, persistent);
-    default: return nullptr;
-  }
-}
-
 void default_props(ode_solver* s) {
   Props& p = s->pr;
   memset(&p, 0, sizeof(p));
@@ -109,7 +112,7 @@ void default_props(ode_solver* s) {
   p.events_on = 0;
   p.td_mode = kTdKeep;
   p.max_steps = 1000000000LL;
-  if (s->model == ODE_DUFFING) {
+  if (s->model == ODE_DUFFING || s->model == ODE_DUFFING_LYAPUNOV) {
     p.mc[0] = -1.0;  // delta
     p.mc[1] = 1.0;   // c3
     p.mc[2] = 1.0;   // omega
@@ -401,8 +404,8 @@ int ode_create(ode_solver** out, int model, int scheme, int prec, int n_systems,
     return fail(nullptr, ODE_ERR_INVALID_ARG, "scheme must be ODE_RK4 or ODE_RKCK45");
   if (prec != ODE_FP64 && prec != ODE_FP32_RHS)
     return fail(nullptr, ODE_ERR_INVALID_ARG, "prec must be ODE_FP64 or ODE_FP32_RHS");
-  if (prec == ODE_FP32_RHS && model == ODE_KELLER_MIKSIS)
-    return fail(nullptr, ODE_ERR_INVALID_ARG, "the Keller-Miksis model is binary64 only");
+  if (prec == ODE_FP32_RHS && (model == ODE_KELLER_MIKSIS || model == ODE_DUFFING_LYAPUNOV))
+    return fail(nullptr, ODE_ERR_INVALID_ARG, "the Keller-Miksis and Lyapunov models are binary64 only");
   if (n_systems < 1) return fail(nullptr, ODE_ERR_INVALID_ARG, "n_systems must be >= 1");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -529,7 +532,7 @@ int ode_set_events(ode_solver* s, int enabled, const int* direction, const doubl
 
 int ode_set_model_constants(ode_solver* s, const double* c, int nc) {
   if (check_solver(s)) return ODE_ERR_INVALID_ARG;
-  const int allowed = s->model == ODE_DUFFING ? 3 : 0;
+  const int allowed = (s->model == ODE_DUFFING || s->model == ODE_DUFFING_LYAPUNOV) ? 3 : 0;
   if (nc < 0 || nc > allowed || (nc > 0 && !c))
     return fail(s, ODE_ERR_INVALID_ARG, "wrong number of model constants for this model");
   for (int i = 0; i < nc; i++) {

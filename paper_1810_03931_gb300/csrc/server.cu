@@ -40,26 +40,8 @@ double now_s() {
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-bool dims(int model, int* n, int* P, int* A, int* E) {
-  switch (model) {
-    case ODE_DUFFING: *n = 2; *P = 2; *A = 7; *E = 1; return true;
-    case ODE_KELLER_MIKSIS: *n = 2; *P = 13; *A = 4; *E = 1; return true;
-    case ODE_VALVE: *n = 3; *P = 5; *A = 5; *E = 2; return true;
-    case ODE_BOUNCE: *n = 2; *P = 2; *A = 6; *E = 1; return true;
-    default: return false;
-  }
-}
-
 // One-thread-per-system kernel (no work queue) of a model.
-const void* kernel_of(int model, int scheme, int prec) {
-  switch (model) {
-    case ODE_DUFFING: return kernel_duffing(scheme, prec, 0);
-    case ODE_KELLER_MIKSIS: return kernel_keller_miksis(scheme, prec, 0);
-    case ODE_VALVE: return kernel_valve(scheme, prec, 0);
-    case ODE_BOUNCE: return kernel_bounce(scheme, prec, 0);
-    default: return nullptr;
-  }
-}
+const void* kernel_of(int model, int scheme, int prec) { return kernel_for(model, scheme, prec, 0); }
 
 __global__ void fill_int_kernel(int* p, int n, int v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
@@ -320,7 +302,7 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
   if (!s) return ODE_ERR_INVALID_ARG;
   if (!cfg) return sfail(s, ODE_ERR_INVALID_ARG, "settings are NULL");
   int n, P, A, E;
-  if (!dims(cfg->model, &n, &P, &A, &E)) return sfail(s, ODE_ERR_INVALID_ARG, "unknown model");
+  if (!model_dims(cfg->model, &n, &P, &A, &E)) return sfail(s, ODE_ERR_INVALID_ARG, "unknown model");
   Pool& pl = s->pools[cfg->model];
   if (pl.on) return sfail(s, ODE_ERR_INVALID_ARG, "model already added");
   const void* fn = kernel_of(cfg->model, cfg->scheme, cfg->prec);

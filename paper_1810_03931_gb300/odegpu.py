@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 # enums of include/odegpu.h
-ODE_DUFFING, ODE_KELLER_MIKSIS, ODE_VALVE, ODE_BOUNCE = 0, 1, 2, 3
+ODE_DUFFING, ODE_KELLER_MIKSIS, ODE_VALVE, ODE_BOUNCE, ODE_DUFFING_LYAPUNOV = 0, 1, 2, 3, 4
 ODE_RK4, ODE_RKCK45 = 0, 1
 ODE_FP64, ODE_FP32_RHS = 0, 1
 ODE_TIMEDOMAIN, ODE_STATE, ODE_PARAM, ODE_ACC, ODE_ALL = 1, 2, 4, 8, 15

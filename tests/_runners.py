@@ -12,7 +12,7 @@ import numpy as np
 import oracle as O
 from paper_1810_03931_gb300 import odegpu as G
 
-DIMS = {0: (2, 2, 7, 1), 1: (2, 13, 4, 1), 2: (3, 5, 5, 2), 3: (2, 2, 6, 1)}  # n, P, A, E
+DIMS = {0: (2, 2, 7, 1), 1: (2, 13, 4, 1), 2: (3, 5, 5, 2), 3: (2, 2, 6, 1), 4: (4, 2, 5, 1)}  # n, P, A, E
 
 
 def _second(w):

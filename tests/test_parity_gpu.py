@@ -139,6 +139,79 @@ def test_duffing_rkck_full_size_sampled():
 
 
 # ---------------------------------------------------------------------------
+# Duffing with its polar linearisation (Sec. 7.1.3): per-period ln y3 with the
+# radius reset by the Finalization hook.
+# ---------------------------------------------------------------------------
+def test_duffing_lyapunov_parity():
+    w = W.duffing_lyapunov(N=320, n_transient=12, n_record=6)
+    A, n = 5, 4
+    # continuous records: ln-stretch a4 and the end state (y3 is 1 after reset)
+    # agreement at 100 x rtol: ln y3 integrates the error over a whole period
+    mask, o = _nonchaotic(w, w["n_transient"], w["n_record"], cont_rows=(4, 5, 6, 8), rtol=1e-9,
+                          agree=1e-7)
+    assert mask.mean() > 0.5
+    g = run_gpu(w)
+    assert np.all(g["status"] == 1)
+    np.testing.assert_array_equal(g["records"][:, A + 2], 1.0)
+    _compare_records(g, o, mask, A, n, tol=1e-7, exact_rows=(9,))
+    ratio = g["nacc"][mask] / o["nacc"][mask]
+    assert np.all(np.abs(ratio - 1) < 1e-3)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_duffing_lyapunov_launch_forms_identical(persistent):
+    w = W.duffing_lyapunov(N=200, n_transient=3, n_record=2)
+    base = run_gpu(w, persistent=0, block=64)
+    other = run_gpu(w, persistent=persistent, block=96)
+    for key in ("y", "acc", "records", "nacc"):
+        np.testing.assert_array_equal(base[key], other[key])
+
+
+def test_duffing_lyapunov_linear_oscillator_exponent():
+    # c3 = 0: the exponent of x'' + k x' + x = B cos t is -k / 2; over n
+    # periods the per-time mean of ln y3 carries a bounded term / (n T)
+    w = W.duffing_lyapunov(N=64, n_transient=0, n_record=200, c3=0.0)
+    g = run_gpu(w)
+    k = w["p"][0]
+    lam = g["records"][:, 4].sum(axis=0) / (200 * 2 * math.pi)
+    np.testing.assert_allclose(lam, -k / 2, rtol=0, atol=5e-4)
+
+
+def test_duffing_lyapunov_full_size_sampled():
+    """The Lyapunov sweep at full size (61440 systems, 1024 + 64 periods) in
+    the persistent launch; sampled systems replayed by the oracle.  The
+    tangent angle of an orbit with complex Floquet multipliers is neutrally
+    stable, so its error (and that of the per-period ln-stretch, which
+    depends on it) grows with the horizon: after 1088 periods the oracle at
+    rtol and at rtol / 10 differs there by ~1e-6.  Those two rows are held to
+    10 x that spread; the oscillator's own state and extrema to 100 x rtol."""
+    w = W.duffing_lyapunov()
+    g = run_gpu(w, persistent=1)
+    assert np.all(g["status"] == 1)
+    idx = W.sample_indices(w["N"], 32, corners=(0, 1, w["N"] - 2, w["N"] - 1))
+    ws = W.subset(w, idx)
+    mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(5, 6), rtol=1e-9, agree=1e-7)
+    o2 = run_oracle(ws, NTHREADS, rtol=1e-10, atol=1e-10)
+    assert mask.sum() >= 8
+    rg, ro, ro2 = g["records"][:, :, idx][:, :, mask], o["records"][:, :, mask], o2["records"][:, :, mask]
+    for row in (0, 2, 5, 6):  # max, min of y1; y1, y2
+        np.testing.assert_array_less(np.abs(rg[:, row] - ro[:, row]), 1e-7 * (1 + np.abs(ro[:, row])))
+    np.testing.assert_array_equal(rg[:, 7], 1.0)
+    np.testing.assert_array_equal(rg[:, 9], ro[:, 9])
+    # ln-stretch; reduced angle (differences taken modulo 2 pi)
+    dang = lambda a, b: np.abs(np.remainder(a - b + math.pi, 2 * math.pi) - math.pi)
+    for row, diff in ((4, lambda a, b: np.abs(a - b)), (8, dang)):
+        spread = np.max(diff(ro2[:, row], ro[:, row]))
+        assert spread < 1e-4
+        np.testing.assert_array_less(diff(rg[:, row], ro[:, row]), max(10 * spread, 1e-7))
+    # the exponents of the whole sweep are finite and, on the sampled
+    # periodic points, negative
+    lam = g["records"][:, 4].mean(axis=0) / (2 * math.pi)
+    assert np.all(np.isfinite(lam))
+    assert np.all(lam[idx][mask] < 0)
+
+
+# ---------------------------------------------------------------------------
 # Keller-Miksis (Sec. 2.2, single frequency), grid corners and interior.
 # ---------------------------------------------------------------------------
 def test_keller_miksis_parity():

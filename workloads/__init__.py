@@ -22,6 +22,10 @@ Workloads (the paper's experiments, Sec. 7, at the sizes of the benchmark):
                  events (y2 max, stop 1) and (y1 impact), equilibrium 50,
                  y0 = (0.2, 0, delta), slices of up to 1e3 time units that
                  stop at the next maximum, RKCK45 rtol 1e-9, 1024 + 64
+  duffing_lyapunov  Duffing with its polar linearisation (largest Lyapunov
+                 exponent, Sec. 7.1.3): k in [0.2, 0.3] over 61440 systems,
+                 B = 0.3, y0 = (-0.5, 0.1, 1, 0), RKCK45 rtol = atol = 1e-9,
+                 slices of one forcing period, 1024 + 64 periods
   serving_mix    Poisson stream of sweep requests over the three models
 """
 from __future__ import annotations
@@ -30,7 +34,7 @@ import math
 
 import numpy as np
 
-DUFFING, KELLER_MIKSIS, VALVE, BOUNCE = 0, 1, 2, 3
+DUFFING, KELLER_MIKSIS, VALVE, BOUNCE, DUFFING_LYAPUNOV = 0, 1, 2, 3, 4
 RK4, RKCK45 = 0, 1
 TD_KEEP, TD_T0_TO_T, TD_SHIFT = 0, 1, 2
 
@@ -68,6 +72,18 @@ def duffing_rkck(nk=512, nB=256, n_transient=1024, n_record=64, events=True):
                  p=np.vstack([kk.ravel(), BB.ravel()]), mc=(-1.0, 1.0, 1.0), events_on=events,
                  evt_dir=(-1,), evt_tol=(1e-12,), evt_stop=(0,), n_transient=n_transient,
                  n_record=n_record)
+
+
+def duffing_lyapunov(N=61440, n_transient=1024, n_record=64, c3=1.0):
+    """Sec. 7.1.3 (Table 4, the largest of its thread counts): each record
+    holds a4 = ln y3 over one period; the exponent is their mean / (2 pi).
+    c3 = 0 gives the linear oscillator, whose exponent is -k / 2."""
+    k = np.linspace(0.2, 0.3, N)
+    B = np.full(N, 0.3)
+    return _base(name="duffing_lyapunov_%d" % N, model=DUFFING_LYAPUNOV, scheme=RKCK45, N=N, h0=1e-2,
+                 rtol=1e-9, atol=1e-9, td=np.vstack([np.zeros(N), np.full(N, 2 * math.pi)]),
+                 y0=np.vstack([np.full(N, -0.5), np.full(N, 0.1), np.ones(N), np.zeros(N)]),
+                 p=np.vstack([k, B]), mc=(-1.0, c3, 1.0), n_transient=n_transient, n_record=n_record)
 
 
 def keller_miksis(npa=512, nf=512, n_transient=1024, n_record=64, pa_max=2.0e5):
