@@ -50,29 +50,62 @@ struct StageType<kFP32RHS> { using type = float; };
 
 // ---- harmonic forcing ------------------------------------------------------
 // For a stage at t + c h the forcing angle advances by c x with x = omega h.
-// cos(c x) and sin(c x) come from their Taylor series to degree 8 and 9 in x,
-// with the powers of c folded into compile-time coefficients, as polynomials
-// in U = x^2 (the first omitted terms are below 3e-17 relative for |x| <= 0.1):
-//   cos(c x) = 1 + U (a1 + U (a2 + U (a3 + U a4))),  a_k = (-1)^k c^2k / (2k)!
-//   sin(c x) = x (b0 + U (b1 + U (b2 + U (b3 + U b4)))), b_k = (-1)^k c^(2k+1) / (2k+1)!
+// For |x| <= kSmallAngle = 0.1, cos(c x) and sin(c x) / x are cubics in
+// U = x^2 with the powers of c folded into compile-time coefficients: the
+// Taylor series to U^4 (a_k = (-1)^k c^2k / (2k)!, b_k = (-1)^k c^(2k+1) /
+// (2k+1)!; the U^5 terms are below 3e-17) with its U^4 term replaced by the
+// best cubic approximation of U^4 on one of two intervals, [0, U1] and
+// [U1, kSmallAngle^2] with U1 = 0.07^2 (Chebyshev economization, Lanczos):
+// on [m - w, m + w], U^4 = r(U) + (w^4 / 8) T4((U - m) / w) with
+//   r(U) = 4 m U^3 + (w^2 - 6 m^2) U^2 + (4 m^3 - 2 m w^2) U
+//          + m^2 w^2 - m^4 - w^4 / 8,
+// so the replacement adds at most |a4| w^4 / 8 (1.3e-16 for cos at c = 1).
+// The interval is chosen per lane by selecting coefficients (no branch).
+// Larger angles call sincos.
+constexpr double kSmallAngle = 0.1;
+constexpr double kU1 = 0.07 * 0.07;
+
 __host__ __device__ constexpr double cpow(double c, int k) { return k == 0 ? 1.0 : c * cpow(c, k - 1); }
 __host__ __device__ constexpr double fact(int k) { return k <= 1 ? 1.0 : k * fact(k - 1); }
 __host__ __device__ constexpr double cos_coef(double c, int k) { return (k % 2 ? -1.0 : 1.0) * cpow(c, 2 * k) / fact(2 * k); }
 __host__ __device__ constexpr double sin_coef(double c, int k) {
   return (k % 2 ? -1.0 : 1.0) * cpow(c, 2 * k + 1) / fact(2 * k + 1);
 }
-
-template <int CNUM, int CDEN>
-__device__ __forceinline__ void small_angle_c(double x, double U, double& cd, double& sd) {
-  constexpr double c = (double)CNUM / (double)CDEN;
-  constexpr double a1 = cos_coef(c, 1), a2 = cos_coef(c, 2), a3 = cos_coef(c, 3), a4 = cos_coef(c, 4);
-  constexpr double b0 = sin_coef(c, 0), b1 = sin_coef(c, 1), b2 = sin_coef(c, 2), b3 = sin_coef(c, 3),
-                   b4 = sin_coef(c, 4);
-  cd = fma(fma(fma(fma(U, a4, a3), U, a2), U, a1), U, 1.0);
-  sd = x * fma(fma(fma(fma(U, b4, b3), U, b2), U, b1), U, b0);
+// coefficient j (0..3) of the cubic economized from the quartic with U^j
+// coefficient aj and U^4 coefficient a4 on [m - w, m + w]
+__host__ __device__ constexpr double econ3(double aj, double a4, int j, double m, double w) {
+  return j == 3 ? aj + a4 * 4.0 * m
+       : j == 2 ? aj + a4 * (w * w - 6.0 * m * m)
+       : j == 1 ? aj + a4 * (4.0 * m * m * m - 2.0 * m * w * w)
+                : aj + a4 * (m * m * w * w - cpow(m, 4) - cpow(w, 4) / 8.0);
 }
 
-constexpr double kSmallAngle = 0.1;
+// Coefficients of cos(c x) (a0..a3) and sin(c x) / x (b0..b3) on interval I
+// (0: [0, U1], 1: [U1, kSmallAngle^2]).
+template <int CNUM, int CDEN, int I>
+struct AngleCubic {
+  static constexpr double c = (double)CNUM / (double)CDEN;
+  static constexpr double lo = I == 0 ? 0.0 : kU1, hi = I == 0 ? kU1 : kSmallAngle * kSmallAngle;
+  static constexpr double m = 0.5 * (lo + hi), w = 0.5 * (hi - lo);
+  static constexpr double a4 = cos_coef(c, 4), b4 = sin_coef(c, 4);
+  static constexpr double a0 = econ3(1.0, a4, 0, m, w), a1 = econ3(cos_coef(c, 1), a4, 1, m, w),
+                          a2 = econ3(cos_coef(c, 2), a4, 2, m, w), a3 = econ3(cos_coef(c, 3), a4, 3, m, w);
+  static constexpr double b0 = econ3(sin_coef(c, 0), b4, 0, m, w), b1 = econ3(sin_coef(c, 1), b4, 1, m, w),
+                          b2 = econ3(sin_coef(c, 2), b4, 2, m, w), b3 = econ3(sin_coef(c, 3), b4, 3, m, w);
+};
+
+// cd = cos(c x), sd = sin(c x) for |x| <= kSmallAngle; lo: U <= U1
+template <int CNUM, int CDEN>
+__device__ __forceinline__ void small_angle_c(double x, double U, bool lo, double& cd, double& sd) {
+  using L = AngleCubic<CNUM, CDEN, 0>;
+  using H = AngleCubic<CNUM, CDEN, 1>;
+  const double a3 = lo ? L::a3 : H::a3, a2 = lo ? L::a2 : H::a2, a1 = lo ? L::a1 : H::a1,
+               a0 = lo ? L::a0 : H::a0;
+  const double b3 = lo ? L::b3 : H::b3, b2 = lo ? L::b2 : H::b2, b1 = lo ? L::b1 : H::b1,
+               b0 = lo ? L::b0 : H::b0;
+  cd = fma(fma(fma(U, a3, a2), U, a1), U, a0);
+  sd = x * fma(fma(fma(U, b3, b2), U, b1), U, b0);
+}
 
 // (sin, cos)(a) in binary32 for a binary64 angle a: a is reduced to
 // r = a - k pi/2 in [-pi/4, pi/4] in binary64 (k = rint(a 2/pi) by adding
@@ -135,21 +168,22 @@ struct Stepper {
   template <int CNUM, int CDEN>
   static __device__ __forceinline__ Stage<T> stage_at(double t, double hs, T tb, T h,
                                                       const T (&mct)[3], T C, T S, double w,
-                                                      double x, double U, bool small, T xw) {
+                                                      double x, double U, bool small, bool lo,
+                                                      T xw) {
     constexpr double c = (double)CNUM / (double)CDEN;
     Stage<T> st;
     if constexpr (kRotate) {
       st.t = t + c * hs;
       if (small) {
         double cd, sd;
-        small_angle_c<CNUM, CDEN>(x, U, cd, sd);
+        small_angle_c<CNUM, CDEN>(x, U, lo, cd, sd);
         st.c = C * cd - S * sd;
         st.s = S * cd + C * sd;
       } else {
         sincos(w * st.t, &st.s, &st.c);
       }
     } else {
-      (void)mct; (void)U;
+      (void)mct; (void)U; (void)lo;
       st.t = tb + (T)c * h;
       if constexpr (M::kForcing != kNoForcing) {
         if (small) {
@@ -161,7 +195,7 @@ struct Stepper {
           sincos_quarter(fma(c, w * hs, w * t), st.s, st.c);
         }
       } else {
-        (void)t; (void)hs; (void)C; (void)S; (void)w; (void)x; (void)small; (void)xw;
+        (void)t; (void)hs; (void)C; (void)S; (void)w; (void)x; (void)small; (void)lo; (void)xw;
         st.c = st.s = (T)0;
       }
     }
@@ -180,6 +214,7 @@ struct Stepper {
     const T tb = (T)t;
     const double x = w * hs, U = x * x;
     const bool small = fabs(x) <= kSmallAngle;
+    const bool lo = dbits(U) <= dbits(kU1);  // U >= 0: compared on the integer pipe
     const T xw = (!kRotate && M::kForcing != kNoForcing) ? (T)x : (T)0;
     T ys[n];
     if constexpr (SCHEME == kRKCK45) {
@@ -187,19 +222,19 @@ struct Stepper {
       T k2[n], k3[n], k4[n], k5[n], k6[n];
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a21 * k1[m]);
-      M::template rhs<T>(stage_at<1, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k2);
+      M::template rhs<T>(stage_at<1, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw), ys, pt, mct, k2);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, (T)a31 * k1[m] + (T)a32 * k2[m]);
-      M::template rhs<T>(stage_at<3, 10>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k3);
+      M::template rhs<T>(stage_at<3, 10>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw), ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h, (T)a41 * k1[m] + (T)a42 * k2[m] + (T)a43 * k3[m]);
-      M::template rhs<T>(stage_at<3, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k4);
+      M::template rhs<T>(stage_at<3, 5>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw), ys, pt, mct, k4);
 #pragma unroll
       for (int m = 0; m < n; m++)
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a51 * k1[m] + (T)a52 * k2[m] + (T)a53 * k3[m] + (T)a54 * k4[m]);
-      const Stage<T> s5 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
+      const Stage<T> s5 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
       M::template rhs<T>(s5, ys, pt, mct, k5);
       Cn = (double)s5.c;
       Sn = (double)s5.s;
@@ -208,7 +243,7 @@ struct Stepper {
         ys[m] = stage(y[m], yb[m], hs, h,
                       (T)a61 * k1[m] + (T)a62 * k2[m] + (T)a63 * k3[m] + (T)a64 * k4[m] +
                           (T)a65 * k5[m]);
-      M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small, xw), ys, pt, mct, k6);
+      M::template rhs<T>(stage_at<7, 8>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw), ys, pt, mct, k6);
 #pragma unroll
       for (int m = 0; m < n; m++) {
         // binary64 state update and error estimate; with binary32 stages the
@@ -222,7 +257,7 @@ struct Stepper {
     } else {
       T k2[n], k3[n], k4[n];
       const T half = (T)0.5;
-      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
+      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
       M::template rhs<T>(sh, ys, pt, mct, k2);
@@ -231,7 +266,7 @@ struct Stepper {
       M::template rhs<T>(sh, ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
-      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, xw);
+      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
       M::template rhs<T>(s4, ys, pt, mct, k4);
       Cn = (double)s4.c;
       Sn = (double)s4.s;
@@ -339,7 +374,7 @@ struct Lane {
 
   // Load the slot; false when the system has no slice to run in this launch.
   __device__ __forceinline__ bool load(const KArgs& a) {
-    const int N = a.ld;
+    const size_t N = (size_t)a.ld;  // 64-bit component offsets
     my_slices = a.n_slices;
     if (a.slices_left != nullptr) my_slices = min(my_slices, a.slices_left[sys]);
     if (my_slices <= 0) return false;
@@ -359,7 +394,7 @@ struct Lane {
   }
 
   __device__ __forceinline__ void store(const KArgs& a) {
-    const int N = a.ld;
+    const size_t N = (size_t)a.ld;  // 64-bit component offsets
     a.td[sys] = t0;
     a.td[N + sys] = t1;
 #pragma unroll
