@@ -284,12 +284,15 @@ def test_valve_parity(persistent):
     _valve_compare(g, o, stable, tol)
 
 
-def test_valve_parity_paper_event_tolerance():
+@pytest.mark.parametrize("rtol", [1e-9, 1e-10], ids=["rtol1e-9", "paper_rtol1e-10"])
+def test_valve_parity_paper_event_tolerance(rtol):
     """The paper's event tolerance 1e-6 (Sec. 6.6): a located point is fixed
-    only to |F| <= 1e-6, so the acceptance is 100 x that tolerance."""
-    w = W.valve(N=96, n_transient=30, n_record=10)
+    only to |F| <= 1e-6, so the acceptance is 100 x that tolerance; at the
+    benchmark's rtol 1e-9 and at the paper's own valve run, rtol = atol =
+    1e-10 (Sec. 7.3)."""
+    w = W.valve(N=96, n_transient=30, n_record=10, rtol=rtol)
     o = run_oracle(w, NTHREADS)
-    o2 = run_oracle(w, NTHREADS, rtol=1e-10, atol=1e-10)
+    o2 = run_oracle(w, NTHREADS, rtol=rtol / 10, atol=rtol / 10)
     tol = 100 * w["evt_tol"][0]
     stable = _valve_stable(w, o, o2, tol)
     assert stable.sum() >= 75
