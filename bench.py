@@ -152,6 +152,35 @@ def rank_band(w, rank):
     return w
 
 
+def kernel_source_digest():
+    """sha256 over the integrator's CUDA sources and the ABI header: a DRAM
+    traffic figure measured by ncu applies only to the sources it was taken
+    on."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1810_03931_gb300", "csrc")
+    files = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in files + ["../../include/odegpu.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload_name, launch):
+    """DRAM bytes (read + write) of one integrator launch of this workload
+    and launch form, from the ncu summary committed under profiles/ -- or None
+    when it was taken on other sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        table = json.load(f)
+    e = table.get(workload_name, {}).get("persistent" if launch else "per_sweep")
+    if not e or e.get("source_sha256") != kernel_source_digest():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
 def reduce_over_ranks(steps, ms, e2e_steps, e2e_s, world, device):
     """Whole-job numbers: (sum of accepted steps, max time in ms, end-to-end
     rate = sum of steps / max end-to-end time).  One collective per quantity
@@ -352,7 +381,9 @@ def run_gpu(args):
                     "s_per_step": float(np.mean(e2e_times)) if e2e_times else None},
             "gpu_launches": args.steps,  # one integrator launch per step
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": args.traffic,
+                         "frac": achieved_tflops / peak_tflops,
+                         "traffic": args.traffic if args.traffic is not None
+                         else measured_traffic(w["name"], args.persistent),
                          "peak_basis": "2 FP64 FMA/clk/SM x %d SMs x %.0f MHz x 2 (derived; live probe %.3f TFLOP/s)"
                                        % (sms, max_mhz, 2 * dfma / 1e12),
                          "flops_per_step": per_step, "arith_flops_per_step": arith,

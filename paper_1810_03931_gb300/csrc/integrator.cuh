@@ -20,6 +20,8 @@
 //    properties come from the kernel parameter block.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "bits.cuh"
 #include "common.cuh"
 #include "models.cuh"
@@ -814,9 +816,22 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
     L.w = M::omega(mcd);
   }
 
+  // Persistent form: systems come from the device queue in warp-aggregated
+  // pops -- the lanes that ask together take consecutive indices, so a warp
+  // works on neighbouring systems of the parameter grid (similar step counts:
+  // the "clustering" of Sec. 7.2) instead of an arbitrary interleaving of
+  // per-lane atomics.
+  auto pop = [&]() -> int {
+    namespace cg = cooperative_groups;
+    const cg::coalesced_group g = cg::coalesced_threads();
+    unsigned int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(a.queue_head, g.size());
+    base = g.shfl(base, 0);
+    return (int)(base + g.thread_rank());
+  };
   bool active;
   if constexpr (PERSIST) {
-    L.sys = (int)atomicAdd(a.queue_head, 1u);
+    L.sys = pop();
   } else {
     L.sys = blockIdx.x * blockDim.x + threadIdx.x;
   }
@@ -827,7 +842,7 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
   // a slice to integrate or no work at all.
   auto next_system = [&]() {
     if constexpr (PERSIST) {
-      L.sys = (int)atomicAdd(a.queue_head, 1u);
+      L.sys = pop();
       active = L.sys < a.N;
       fresh = active;
     } else {
