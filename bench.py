@@ -225,11 +225,19 @@ def run_gpu(args):
     from _runners import DIMS, km_params_gpu
 
     w = workload(args.workload, rank)
-    if args.order == "shuffled":
+    if args.order in ("shuffled", "clustered"):
         # the same systems in a seeded random order: neighbouring lanes no
         # longer share similar parameters (the "clustering" remark of Sec. 7.2)
         perm = np.random.default_rng(W.SEED).permutation(w["N"])
         w = dict(W.subset(w, perm), name=w["name"] + "_shuffled")
+    if args.order == "clustered":
+        # ... then put back in order by the library's Z-order of the swept
+        # parameters
+        if w["model"] == W.KELLER_MIKSIS:
+            keys = np.vstack([w[k] for k in ("PA", "omega", "PA2", "omega2") if k in w])
+        else:
+            keys = w["p"][np.ptp(w["p"], axis=1) > 0]
+        w = dict(W.subset(w, G.ode_cluster_order(keys)), name=w["name"] + "_clustered")
     if args.n_transient is not None:
         w["n_transient"] = args.n_transient
     if args.n_record is not None:
@@ -623,8 +631,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--order", default="grid", choices=["grid", "shuffled"],
-                    help="system order: parameter grid (neighbours similar) or seeded shuffle")
+    ap.add_argument("--order", default="grid", choices=["grid", "shuffled", "clustered"],
+                    help="system order: parameter grid, seeded shuffle, or shuffle then ode_cluster_order")
     ap.add_argument("--n-transient", type=int, default=None, help="override (profiling runs)")
     ap.add_argument("--n-record", type=int, default=None, help="override (profiling runs)")
     args = ap.parse_args()

@@ -268,6 +268,20 @@ int ode_km_coefficients(double PA1, double PA2, double omega1, double omega2, do
                         double RE, double Pinf, double pV, double sigma, double mu, double rho,
                         double cL, double gamma, double *C);
 
+/* Clustering order (Sec. 7.2: threads of a warp should integrate systems of
+ * similar parameters, which need similar numbers of steps).  keys: host array
+ * [K][N] (component-major, K in 1..8) of the quantities that govern the step
+ * counts, e.g. the swept parameters.  perm: host array of N ints that
+ * receives a permutation of 0..N-1 visiting the systems along a Z-order
+ * (Morton) curve of the keys, each scaled to [0, 1] over its finite range
+ * and quantized to floor(63 / K) bits (at most 31); keys with no spread are
+ * ignored, systems with a non-finite key come last, ties keep index order.
+ * Load system perm[i] into slot i (e.g. ode_random_set) so that neighbouring
+ * slots -- one warp, and consecutive pops of the persistent work queue --
+ * hold neighbouring parameter points.  Pure host computation; the paper has
+ * no such call (it leaves the ordering to the user). */
+int ode_cluster_order(const double *keys, int K, int N, int *perm);
+
 /* Kernel resources of one (model, scheme, prec, persistent) instantiation:
  * registers per thread, local (spill) bytes per thread, and the resident
  * blocks per SM at the given block size.  Any output may be NULL. */

@@ -32,7 +32,7 @@ SYMBOLS = (
     "ode_set_events", "ode_set_model_constants", "ode_set_time_domain_mode", "ode_set_step_budget",
     "ode_set_time_limit", "ode_set_launch", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
     "ode_solve", "ode_run_periods", "ode_autotune", "ode_synchronize", "ode_get_status", "ode_reset_counters",
-    "ode_last_error", "ode_km_coefficients", "ode_kernel_info", "ode_probe_fma_peak",
+    "ode_last_error", "ode_km_coefficients", "ode_cluster_order", "ode_kernel_info", "ode_probe_fma_peak",
     "ode_probe_call_cost", "ode_run_periods_noalloc",
     "ode_server_create", "ode_server_add_model", "ode_server_submit", "ode_server_progress",
     "ode_server_poll", "ode_server_result", "ode_server_destroy", "ode_server_last_error",
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
         "ode_reset_counters": [_vp, _vp],
         "ode_last_error": [_vp],
         "ode_km_coefficients": [d] * 13 + [_dp],
+        "ode_cluster_order": [_dp, i, i, _ip],
         "ode_kernel_info": [i, i, i, i, i, i, _ip, _ip, _ip],
         "ode_probe_fma_peak": [i, _dp, _dp],
         "ode_probe_call_cost": [i, _dp, _dp],
@@ -316,6 +317,15 @@ def ode_km_coefficients(PA1, PA2, omega1, omega2, theta, RE, Pinf, pV, sigma, mu
     _check(load().ode_km_coefficients(PA1, PA2, omega1, omega2, theta, RE, Pinf, pV, sigma, mu, rho,
                                       cL, gamma, C.ctypes.data_as(_dp)))
     return C
+
+
+def ode_cluster_order(keys):
+    """Permutation of the N systems along a Z-order curve of `keys` (K x N):
+    slot i should hold system perm[i]."""
+    k = np.ascontiguousarray(np.atleast_2d(np.asarray(keys, dtype=np.float64)))
+    perm = np.zeros(k.shape[1], dtype=np.int32)
+    _check(load().ode_cluster_order(k.ctypes.data_as(_dp), k.shape[0], k.shape[1], perm.ctypes.data_as(_ip)))
+    return perm
 
 
 def ode_kernel_info(model, scheme, prec, persistent=0, block_size=0, device=0):

@@ -90,3 +90,41 @@ def test_workload_generators_are_seeded_and_shaped():
     assert all(1 <= r["size"] <= 2 ** 16 and 16 <= r["horizon"] <= 1024 for r in s1)
     idx = W.sample_indices(1000, 20, corners=(0, 999))
     assert len(idx) == 20 and 0 in idx and 999 in idx
+
+
+def _morton_reference(keys):
+    """Z-order of the columns of `keys` written independently: each key
+    scaled to [0, 1] over its range, quantized to b = min(31, 63 // K) bits,
+    codes compared as bit strings interleaved most significant first."""
+    K, N = keys.shape
+    b = min(31, 63 // K)
+    q = np.zeros((K, N), dtype=np.int64)
+    for d in range(K):
+        lo, hi = keys[d].min(), keys[d].max()
+        if hi > lo:
+            q[d] = np.floor((keys[d] - lo) / (hi - lo) * (2 ** b - 1) + 0.5).astype(np.int64)
+    def code(i):
+        return tuple((int(q[d, i]) >> bit) & 1 for bit in reversed(range(b)) for d in reversed(range(K)))
+    return sorted(range(N), key=lambda i: (code(i), i))
+
+
+def test_cluster_order_is_a_z_order_permutation():
+    rng = np.random.default_rng(7)
+    for K, N in ((1, 50), (2, 300), (3, 200)):
+        keys = rng.random((K, N))
+        keys[0, :5] = keys[0, 5]  # ties keep index order
+        perm = G.ode_cluster_order(keys)
+        assert list(perm) == _morton_reference(keys)
+    # a constant key orders nothing; non-finite keys go last
+    k = np.vstack([np.linspace(0, 1, 8)[::-1], np.full(8, 3.0)])
+    assert list(G.ode_cluster_order(k)) == list(range(8))[::-1]
+    k = np.array([[0.5, np.nan, 0.1, np.inf, 0.9]])
+    assert list(G.ode_cluster_order(k)) == [2, 0, 4, 1, 3]
+    # neighbours in the order are close in parameter space
+    g = np.stack(np.meshgrid(np.linspace(0, 1, 32), np.linspace(0, 1, 32))).reshape(2, -1)
+    sh = g[:, rng.permutation(g.shape[1])]
+    cl = sh[:, G.ode_cluster_order(sh)]
+    step = lambda a: np.mean(np.abs(np.diff(a, axis=1)).sum(axis=0))
+    assert step(cl) < 0.1 * step(sh)
+    with pytest.raises(G.ODEError):
+        G.ode_cluster_order(np.zeros((9, 4)))

@@ -300,6 +300,22 @@ def test_valve_parity_paper_event_tolerance(rtol):
     _valve_compare(g, o, stable, tol)
 
 
+def test_cluster_order_keeps_results_per_system():
+    """Reordering the systems (here: shuffled, then put in the library's
+    clustering order) changes which lanes share a warp but no system's
+    result."""
+    w = W.valve(N=256, n_transient=4, n_record=2)
+    ws = W.subset(w, np.random.default_rng(3).permutation(w["N"]))
+    perm = G.ode_cluster_order(ws["p"][3:4])  # the swept flow rate q
+    wc = W.subset(ws, perm)
+    for persistent in (0, 1):
+        gs = run_gpu(ws, persistent=persistent)
+        gc = run_gpu(wc, persistent=persistent)
+        for key in ("y", "acc", "nacc", "status"):
+            np.testing.assert_array_equal(gc[key], gs[key][..., perm], err_msg=key)
+        np.testing.assert_array_equal(gc["records"], gs["records"][..., perm])
+
+
 def test_valve_equilibrium_stop_high_flow_rate():
     """q > 8.5 settles to the equilibrium inside the event-0 zone and stops
     after MaximumIterationForEquilibrium = 50 steps (Sec. 4, Sec. 7.3)."""
