@@ -64,7 +64,9 @@ struct KArgs {
   double h0;
   int* slices_left;          // per-system slices still to run (served pools), or null:
                              // a system runs min(n_slices, slices_left[i]) slices
-  unsigned int* queue_head;  // persistent launches: next system to take
+  unsigned int* queue_head;  // persistent launches: next queue slot to take
+  unsigned int queue_stride; // persistent launches: queue chunk c of 32 slots holds
+                             // systems 32 * ((c * queue_stride) mod chunks) + 0..31
   int* flags;                // flags[0] != 0: the watchdog stopped a system
   long long time_limit_ns;   // per-thread run-time limit of one launch (0 = none)
   Props pr;
@@ -83,6 +85,21 @@ const void* kernel_duffing_lyapunov(int scheme, int prec, int persistent);
 // Model dimensions (n, P, A, E) of the compiled hooks; false for an unknown
 // model.  The kernel of a model for (scheme, precision, launch form), or null.
 bool model_dims(int model, int* n, int* P, int* A, int* E);
+
+// Multiplier for the persistent queue's chunk order: coprime with the number
+// of 32-system chunks and near its golden-ratio fraction, so that chunks
+// popped one after another lie far apart in the system order.
+inline unsigned int queue_stride_for(int n_systems) {
+  const unsigned int chunks = (unsigned int)((n_systems + 31) / 32);
+  if (chunks <= 2) return 1u;
+  unsigned int k = (unsigned int)(0.6180339887498949 * chunks);
+  if (k < 1) k = 1;
+  for (;; k++) {
+    unsigned int a = k, b = chunks;
+    while (b) { const unsigned int r = a % b; a = b; b = r; }
+    if (a == 1) return k;
+  }
+}
 const void* kernel_for(int model, int scheme, int prec, int persistent);
 
 }  // namespace odegpu

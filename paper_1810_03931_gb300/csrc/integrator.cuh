@@ -816,18 +816,28 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
     L.w = M::omega(mcd);
   }
 
-  // Persistent form: systems come from the device queue in warp-aggregated
-  // pops -- the lanes that ask together take consecutive indices, so a warp
+  // Persistent form: the device queue hands out slots in warp-aggregated
+  // pops -- the lanes that ask together take consecutive slots, and slot
+  // 32 c + r holds system 32 ((c * queue_stride) mod chunks) + r.  So a warp
   // works on neighbouring systems of the parameter grid (similar step counts:
-  // the "clustering" of Sec. 7.2) instead of an arbitrary interleaving of
-  // per-lane atomics.
+  // the "clustering" of Sec. 7.2), while chunks popped one after another
+  // (e.g. by the warps of one SM at the start) lie far apart in the grid,
+  // which balances cheap and expensive regions across SMs.
+  const unsigned int chunks = (unsigned int)((a.N + 31) / 32);
   auto pop = [&]() -> int {
     namespace cg = cooperative_groups;
-    const cg::coalesced_group g = cg::coalesced_threads();
-    unsigned int base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(a.queue_head, g.size());
-    base = g.shfl(base, 0);
-    return (int)(base + g.thread_rank());
+    for (;;) {
+      const cg::coalesced_group g = cg::coalesced_threads();
+      unsigned int base = 0;
+      if (g.thread_rank() == 0) base = atomicAdd(a.queue_head, g.size());
+      base = g.shfl(base, 0);
+      const unsigned int q = base + g.thread_rank();
+      const unsigned int c = q >> 5;
+      if (c >= chunks) return a.N;  // queue exhausted
+      const unsigned int pc = (unsigned int)(((unsigned long long)c * a.queue_stride) % chunks);
+      const int sys = (int)(pc * 32u + (q & 31u));
+      if (sys < a.N) return sys;  // else: the unused tail of the last chunk
+    }
   };
   bool active;
   if constexpr (PERSIST) {

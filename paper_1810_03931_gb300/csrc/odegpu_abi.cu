@@ -367,6 +367,7 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.h0 = h0;
   a.slices_left = nullptr;
   a.queue_head = s->d_queue;
+  a.queue_stride = queue_stride_for(s->N);
   a.flags = (int*)((char*)s->d_queue + 64);
   a.time_limit_ns = (long long)(s->time_limit_s * 1e9);
   a.pr = s->pr;

@@ -181,6 +181,7 @@ int build_request_graph(ode_server* s, Pool& pl, Request* r) {
   a.h0 = pl.h0;
   a.slices_left = pl.left + off;
   a.queue_head = nullptr;
+  a.queue_stride = 1u;
   a.flags = (int*)(pl.head + 64);
   a.time_limit_ns = (long long)(pl.time_limit_s * 1e9);
   a.pr = pl.pr;
