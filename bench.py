@@ -616,11 +616,11 @@ def main():
     ap.add_argument("--workload", default="duffing_rkck",
                     choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "duffing_lyapunov",
                              "serving"])
-    ap.add_argument("--requests", type=int, default=60, help="serving: requests per run")
+    ap.add_argument("--requests", type=int, default=40, help="serving: requests per run")
     ap.add_argument("--slice-periods", type=int, default=2, help="serving: periods per tick")
     ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
     ap.add_argument("--max-log2-horizon", type=int, default=10, help="serving: horizons floor(2^U(4, x))")
-    ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 0.8, 1.0])
+    ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 1.0])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32rhs"])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
