@@ -282,6 +282,7 @@ def run_gpu(args):
         tune = {"block": bs, "persistent": pers, "trial_slices": args.tune_slices,
                 "trial_ms": {"per_sweep": [round(x, 2) for x in trials[0]],
                              "persistent": [round(x, 2) for x in trials[1]],
+                             "persistent_lane_order": [round(x, 2) for x in trials[2]],
                              "blocks": [64, 96, 128, 160, 192, 256]}}
         args.persistent = pers
         args.block = bs

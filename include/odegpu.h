@@ -175,10 +175,15 @@ int ode_set_step_budget(ode_solver *s, long long max_steps_per_slice);
  * Default 600 s; 0 disables it.  It bounds the run time of every launch. */
 int ode_set_time_limit(ode_solver *s, double seconds);
 
-/* Launch shape: block_size (multiple of 32 in [32, 1024], 0 = automatic) and
- * persistent (1 = a persistent grid whose threads refill their slot from a
- * device work queue the moment their system finishes; 0 = one thread per
- * system, grid ceil(N / block_size), the launch of Sec. 6.4). */
+/* Launch shape: block_size (multiple of 32 in [32, 256], 0 = automatic) and
+ * persistent: 0 = one thread per system, grid ceil(N / block_size), the
+ * launch of Sec. 6.4; 1 or 2 = a persistent grid (resident blocks x SMs)
+ * whose threads refill their slot from a device work queue the moment their
+ * system finishes.  Queue order 1: warp-aggregated pops of 32 consecutive
+ * systems, chunks handed out in a stride order that spreads consecutive pops
+ * over the index range (a warp holds neighbouring systems, SMs get a mix of
+ * the sweep); order 2: each thread takes the next system in index order.
+ * Results do not depend on the shape. */
 int ode_set_launch(ode_solver *s, int block_size, int persistent);
 
 /* ---- filling and reading the object (Sec. 6.3, 6.10) --------------------- */
@@ -233,13 +238,13 @@ int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, dou
 
 /* Autotuner: integrate n_slices slices from the current state with every
  * launch shape of a fixed candidate list -- block size 64, 96, 128, 160,
- * 192, 256, each per-sweep and persistent (shapes the kernel cannot launch
- * are skipped) -- timed with CUDA events on `stream`, then restore the state,
- * status and counters and keep the fastest shape (as ode_set_launch would).
- * Outputs (may be NULL): the chosen block size and persistent flag, and
- * trial_ms[12] = milliseconds per trial in the order [persistent][block]
- * (-1 for skipped shapes).  Allocates a temporary copy of the state.
- * Synchronous. */
+ * 192, 256, each per-sweep and persistent with queue order 1 and 2 (shapes
+ * the kernel cannot launch are skipped) -- timed with CUDA events on
+ * `stream`, then restore the state, status and counters and keep the fastest
+ * shape (as ode_set_launch would).  Outputs (may be NULL): the chosen block
+ * size and persistent value, and trial_ms[18] = milliseconds per trial in the
+ * order [persistent 0, 1, 2][block] (-1 for skipped shapes).  Allocates a
+ * temporary copy of the state.  Synchronous. */
 int ode_autotune(ode_solver *s, double h0, int n_slices, void *stream, int *block_size,
                  int *persistent, double *trial_ms);
 

@@ -65,8 +65,10 @@ struct KArgs {
   int* slices_left;          // per-system slices still to run (served pools), or null:
                              // a system runs min(n_slices, slices_left[i]) slices
   unsigned int* queue_head;  // persistent launches: next queue slot to take
-  unsigned int queue_stride; // persistent launches: queue chunk c of 32 slots holds
-                             // systems 32 * ((c * queue_stride) mod chunks) + 0..31
+  int queue_mode;            // persistent launches: 1 = warp-aggregated pops of
+                             // strided 32-system chunks, 2 = one pop per lane
+  unsigned int queue_stride; // mode 1: queue chunk c of 32 slots holds systems
+                             // 32 * ((c * queue_stride) mod chunks) + 0..31
   int* flags;                // flags[0] != 0: the watchdog stopped a system
   long long time_limit_ns;   // per-thread run-time limit of one launch (0 = none)
   Props pr;

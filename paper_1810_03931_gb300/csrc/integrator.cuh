@@ -816,16 +816,20 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
     L.w = M::omega(mcd);
   }
 
-  // Persistent form: the device queue hands out slots in warp-aggregated
-  // pops -- the lanes that ask together take consecutive slots, and slot
-  // 32 c + r holds system 32 ((c * queue_stride) mod chunks) + r.  So a warp
-  // works on neighbouring systems of the parameter grid (similar step counts:
-  // the "clustering" of Sec. 7.2), while chunks popped one after another
-  // (e.g. by the warps of one SM at the start) lie far apart in the grid,
-  // which balances cheap and expensive regions across SMs.
+  // Persistent form, two queue orders (the autotuner tries both):
+  //  mode 1: the device queue hands out slots in warp-aggregated pops -- the
+  //    lanes that ask together take consecutive slots, and slot 32 c + r
+  //    holds system 32 ((c * queue_stride) mod chunks) + r.  So a warp works
+  //    on neighbouring systems of the parameter grid (similar step counts:
+  //    the "clustering" of Sec. 7.2), while chunks popped one after another
+  //    (e.g. by the warps of one SM at the start) lie far apart in the grid,
+  //    which balances cheap and expensive regions across SMs;
+  //  mode 2: every lane pops the next system in index order on its own (the
+  //    lanes of a warp hold systems in the order they freed up).
   const unsigned int chunks = (unsigned int)((a.N + 31) / 32);
   auto pop = [&]() -> int {
     namespace cg = cooperative_groups;
+    if (a.queue_mode == 2) return (int)min(atomicAdd(a.queue_head, 1u), (unsigned int)a.N);
     for (;;) {
       const cg::coalesced_group g = cg::coalesced_threads();
       unsigned int base = 0;

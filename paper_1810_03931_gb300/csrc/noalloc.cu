@@ -164,6 +164,7 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   a.n_skip = n_transient;
   a.h0 = h0;
   a.queue_head = (unsigned int*)scratch;
+  a.queue_mode = 1;
   a.queue_stride = queue_stride_for(n_systems);
   a.flags = (int*)(scratch + 64);
   a.time_limit_ns = (long long)(cfg->time_limit_s * 1e9);

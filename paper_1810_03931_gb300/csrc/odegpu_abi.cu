@@ -347,7 +347,7 @@ int check_watchdog(ode_solver* s, cudaStream_t st) {
 }
 
 int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* records, void* stream) {
-  const void* fn = kernel_for(s->model, s->scheme, s->prec, s->persistent);
+  const void* fn = kernel_for(s->model, s->scheme, s->prec, s->persistent ? 1 : 0);
   if (!fn) return fail(s, ODE_ERR_UNSUPPORTED, "no kernel compiled for this model/scheme/precision");
   cudaStream_t st = (cudaStream_t)stream;
   KArgs a;
@@ -367,6 +367,7 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.h0 = h0;
   a.slices_left = nullptr;
   a.queue_head = s->d_queue;
+  a.queue_mode = s->persistent;
   a.queue_stride = queue_stride_for(s->N);
   a.flags = (int*)((char*)s->d_queue + 64);
   a.time_limit_ns = (long long)(s->time_limit_s * 1e9);
@@ -570,8 +571,10 @@ int ode_set_launch(ode_solver* s, int block_size, int persistent) {
   if (check_solver(s)) return ODE_ERR_INVALID_ARG;
   if (block_size != 0 && (block_size < 32 || block_size > 256 || block_size % 32))
     return fail(s, ODE_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
+  if (persistent < 0 || persistent > 2)
+    return fail(s, ODE_ERR_INVALID_ARG, "persistent must be 0 (per-sweep), 1 or 2 (queue orders)");
   s->block_size = block_size;
-  s->persistent = persistent ? 1 : 0;
+  s->persistent = persistent;
   return ODE_OK;
 }
 
@@ -725,8 +728,8 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
   double best = 1e300;
   int best_b = 128, best_p = 1, rc = ODE_OK;
   int max_threads = 1024;
-  for (int pers = 0; pers < 2 && e == cudaSuccess && rc == ODE_OK; pers++) {
-    const void* fn = kernel_for(s->model, s->scheme, s->prec, pers);
+  for (int pers = 0; pers < 3 && e == cudaSuccess && rc == ODE_OK; pers++) {
+    const void* fn = kernel_for(s->model, s->scheme, s->prec, pers ? 1 : 0);
     cudaFuncAttributes at;
     if (fn && cudaFuncGetAttributes(&at, fn) == cudaSuccess) max_threads = at.maxThreadsPerBlock;
     for (int k = 0; k < 6 && e == cudaSuccess; k++) {

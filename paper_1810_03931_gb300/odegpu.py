@@ -287,12 +287,12 @@ def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
 
 
 def ode_autotune(s, h0, n_slices, stream=None):
-    """Returns (block_size, persistent, trial_ms[2][6])."""
+    """Returns (block_size, persistent, trial_ms[3][6])."""
     b, p = ctypes.c_int(), ctypes.c_int()
-    t = np.zeros(12)
+    t = np.zeros(18)
     _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(p),
                                t.ctypes.data_as(_dp)), s)
-    return b.value, p.value, t.reshape(2, 6)
+    return b.value, p.value, t.reshape(3, 6)
 
 
 def ode_synchronize(s):

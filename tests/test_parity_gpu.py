@@ -89,7 +89,7 @@ def test_duffing_rk4_full_size_parity():
         assert np.all(same_t | _rel_close(rg[:, vrow], ro[:, vrow], 1e-12, 1e-12))
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_duffing_rk4_launch_forms_identical(persistent):
     w = W.duffing_rk4(N=333, n_transient=2, n_record=2)
     base = run_gpu(w, persistent=0, block=64)
@@ -158,7 +158,7 @@ def test_duffing_lyapunov_parity():
     assert np.all(np.abs(ratio - 1) < 1e-3)
 
 
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_duffing_lyapunov_launch_forms_identical(persistent):
     w = W.duffing_lyapunov(N=200, n_transient=3, n_record=2)
     base = run_gpu(w, persistent=0, block=64)
@@ -308,7 +308,7 @@ def test_cluster_order_keeps_results_per_system():
     ws = W.subset(w, np.random.default_rng(3).permutation(w["N"]))
     perm = G.ode_cluster_order(ws["p"][3:4])  # the swept flow rate q
     wc = W.subset(ws, perm)
-    for persistent in (0, 1):
+    for persistent in (0, 1, 2):
         gs = run_gpu(ws, persistent=persistent)
         gc = run_gpu(wc, persistent=persistent)
         for key in ("y", "acc", "nacc", "status"):
@@ -579,6 +579,8 @@ def test_invalid_arguments_are_reported():
         with pytest.raises(G.ODEError):
             G.ode_set_launch(s, 48, 0)
         with pytest.raises(G.ODEError):
+            G.ode_set_launch(s, 64, 3)
+        with pytest.raises(G.ODEError):
             G.ode_solve(s, -1.0)
         with pytest.raises(G.ODEError):
             G.ode_set_events(s, 1, [2], [1e-6], [0], 0)
@@ -621,7 +623,8 @@ def test_autotune_restores_state_and_keeps_results():
     try:
         gpu_load(s, w)
         bs, pers, trials = G.ode_autotune(s, w["h0"], 2)
-        assert bs in (64, 96, 128, 160, 192, 256) and pers in (0, 1)
+        assert bs in (64, 96, 128, 160, 192, 256) and pers in (0, 1, 2)
+        assert trials.shape == (3, 6)
         assert np.all(trials[trials >= 0] > 0) and trials.max() > 0
         rec = np.zeros((2, 10, w["N"]))
         G.ode_run_periods(s, w["h0"], 2, 2, rec)
