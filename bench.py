@@ -79,7 +79,8 @@ def workload(name, rank=0):
 def describe(w, persistent, l2):
     d = {"workload": w["name"], "systems": w["N"], "periods": w["n_transient"] + w["n_record"],
          "recorded_periods": w["n_record"], "scheme": "RKCK45" if w["scheme"] == 1 else "RK4",
-         "rtol": w["rtol"], "launch": "persistent work queue" if persistent else "one thread per system",
+         "rtol": w["rtol"], "launch": {0: "one thread per system", 1: "persistent work queue (clustered chunks)",
+                    2: "persistent work queue (lane order)"}[persistent],
          "l2": l2}
     if w["events_on"]:
         d["events"] = "y2=0 dir -1 located to %g" % w["evt_tol"][0] if w["model"] == 0 else "2 events"
@@ -175,7 +176,7 @@ def measured_traffic(workload_name, launch):
         return None
     with open(path) as f:
         table = json.load(f)
-    e = table.get(workload_name, {}).get("persistent" if launch else "per_sweep")
+    e = table.get(workload_name, {}).get({0: "per_sweep", 1: "persistent", 2: "persistent_lane_order"}[launch])
     if not e or e.get("source_sha256") != kernel_source_digest():
         return None
     return float(e["dram_bytes_per_launch"])
