@@ -332,8 +332,8 @@ typedef struct ode_noalloc_settings {
  * in HBM (the pools together must fit in the server's HBM budget: admission
  * by footprint).  A request of n systems and n_periods periods waits (FIFO per
  * model) until a contiguous range of n free slots exists, is then copied into
- * it and stays resident there.  It advances in chunks of slice_periods slices,
- * each one launch over its slot range (a CUDA graph captured at admission and
+ * it and stays resident there.  It advances in chunks of slices, each one
+ * launch over its slot range (a CUDA graph captured at admission and
  * replayed) on one of the server's streams; chunks of different requests and
  * models run concurrently and a request's next chunk starts as soon as its
  * previous one completes.  When its horizon is done a request is copied out
@@ -343,7 +343,9 @@ typedef struct ode_noalloc_settings {
  * The caller drives the loop with ode_server_progress (non-blocking). */
 typedef struct ode_server ode_server;
 
-/* device, HBM budget for the pools (bytes), slices per chunk (>= 1). */
+/* device, HBM budget for the pools (bytes), slices per chunk: >= 1 fixed, or
+ * 0 = tuned per request (every chunk is timed and the next one sized to take
+ * about 25 ms; the first chunk is one slice). */
 int ode_server_create(ode_server **out, int device, long long hbm_budget_bytes, int slice_periods);
 
 /* Serve a model with the settings of ode_run_periods_noalloc (the settings'

@@ -87,6 +87,7 @@ const void* kernel_duffing_lyapunov(int scheme, int prec, int persistent);
 // Model dimensions (n, P, A, E) of the compiled hooks; false for an unknown
 // model.  The kernel of a model for (scheme, precision, launch form), or null.
 bool model_dims(int model, int* n, int* P, int* A, int* E);
+constexpr int kNumModels = 5;  // model ids 0 .. kNumModels - 1 (enum ode_model)
 
 // Multiplier for the persistent queue's chunk order: coprime with the number
 // of 32-system chunks and near its golden-ratio fraction, so that chunks

@@ -5,9 +5,13 @@
 // model, each integrated for a number of periods (slices) -- is admitted when
 // a contiguous range of free slots exists; its inputs are copied into the
 // range and its state stays resident there until its horizon is done.  An
-// admitted request advances in chunks of `slice_periods` slices: each chunk is
-// one launch of the integrator over the request's slot range (captured once as
-// a CUDA graph at admission and replayed), on one of the server's streams.
+// admitted request advances in chunks of slices: each chunk is one launch of
+// the integrator over the request's slot range (captured once as a CUDA graph
+// at admission and replayed), on one of the server's streams.  The chunk
+// length is fixed (`slice_periods`) or tuned per request (slice_periods = 0):
+// each chunk is timed with events and the next one is sized so that a chunk
+// takes about kChunkTargetMs -- long enough to amortise the launch and the
+// host's polling, short enough that a finished request is noticed soon.
 // Chunks of different requests and models run concurrently on the device; a
 // request's next chunk is launched as soon as its previous chunk completes,
 // so requests never wait for each other's slow systems.  A finished request is
@@ -55,6 +59,12 @@ struct Request {
   int n = 0;
   int periods = 0;
   int scheduled = 0;  // periods enqueued in chunks so far
+  int chunk = 1;      // slices in the next chunk
+  int graph_chunk = 0;  // slices the instantiated graph runs
+  cudaGraph_t graph_def = nullptr;  // the captured graph (kept: owns the node)
+  cudaGraphNode_t node = nullptr;    // its kernel node
+  cudaKernelNodeParams kp;           // the node's launch (function, grid, block)
+  KArgs args;                        // its arguments (n_slices updated per chunk)
   int off = -1;       // first slot
   int state = kWaiting;
   bool harvesting = false;
@@ -66,6 +76,7 @@ struct Request {
   long long* h_acc_steps = nullptr;
   cudaEvent_t done_ev = nullptr;   // results copied out
   cudaEvent_t chunk_ev = nullptr;  // last chunk finished
+  cudaEvent_t start_ev = nullptr;  // last chunk started (tuned chunk length)
   cudaStream_t stream = nullptr;   // borrowed from the server's stream set
   cudaGraphExec_t graph = nullptr; // one chunk of this request
   bool chunk_inflight = false;
@@ -91,6 +102,8 @@ struct Pool {
 };
 
 constexpr int kStreams = 32;
+constexpr double kChunkTargetMs = 25.0;  // tuned chunks: aimed duration
+constexpr int kMaxChunk = 4096;
 
 }  // namespace
 
@@ -99,7 +112,7 @@ struct ode_server {
   int slice_periods = 1;
   long long budget = 0;
   long long used = 0;
-  Pool pools[4];
+  Pool pools[kNumModels];
   cudaStream_t streams[kStreams] = {};
   int next_stream = 0;
   std::map<long long, Request*> reqs;
@@ -176,8 +189,8 @@ int build_request_graph(ode_server* s, Pool& pl, Request* r) {
   a.nacc = pl.nacc + off;
   a.nrej = pl.nrej + off;
   a.records = nullptr;
-  a.n_slices = s->slice_periods;
-  a.n_skip = s->slice_periods;
+  a.n_slices = r->chunk;
+  a.n_skip = r->chunk;
   a.h0 = pl.h0;
   a.slices_left = pl.left + off;
   a.queue_head = nullptr;
@@ -197,11 +210,14 @@ int build_request_graph(ode_server* s, Pool& pl, Request* r) {
   kp.blockDim = dim3(block);
   kp.sharedMemBytes = 0;
   kp.kernelParams = args;
-  cudaGraphNode_t node;
-  cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
+  cudaError_t e = cudaGraphAddKernelNode(&r->node, g, nullptr, 0, &kp);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&r->graph, g, 0);
-  cudaGraphDestroy(g);
+  r->graph_def = g;  // kept with the request: its node is updated per chunk
   if (e != cudaSuccess) return scuda(s, e, "chunk graph");
+  r->kp = kp;
+  r->kp.kernelParams = nullptr;
+  r->args = a;
+  r->graph_chunk = r->chunk;
   return ODE_OK;
 }
 
@@ -212,18 +228,43 @@ void free_request(Request* r) {
   if (r->h_acc_steps) cudaFreeHost(r->h_acc_steps);
   if (r->done_ev) cudaEventDestroy(r->done_ev);
   if (r->chunk_ev) cudaEventDestroy(r->chunk_ev);
+  if (r->start_ev) cudaEventDestroy(r->start_ev);
   if (r->graph) cudaGraphExecDestroy(r->graph);
+  if (r->graph_def) cudaGraphDestroy(r->graph_def);
   delete r;
 }
 
 // Copy a request's inputs into its slot range and arm its slice count.
 int launch_chunk(ode_server* s, Pool& pl, Request* r) {
+  if (r->chunk != r->graph_chunk) {
+    // same node, new slice count: update the executable graph in place
+    r->args.n_slices = r->chunk;
+    r->args.n_skip = r->chunk;
+    void* args[] = {&r->args};
+    cudaKernelNodeParams kp = r->kp;
+    kp.kernelParams = args;
+    SCK(s, cudaGraphExecKernelNodeSetParams(r->graph, r->node, &kp));
+    r->graph_chunk = r->chunk;
+  }
+  if (s->slice_periods == 0) SCK(s, cudaEventRecord(r->start_ev, r->stream));
   SCK(s, cudaGraphLaunch(r->graph, r->stream));
   SCK(s, cudaEventRecord(r->chunk_ev, r->stream));
   r->chunk_inflight = true;
-  r->scheduled += s->slice_periods;
+  r->scheduled += r->chunk;
   pl.chunks++;
   return ODE_OK;
+}
+
+// Tuned chunk length: scale the last chunk's slice count towards the target
+// duration (at most 4x up or down per step).
+void retune_chunk(Request* r) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, r->start_ev, r->chunk_ev) != cudaSuccess || !(ms > 0.f)) return;
+  double f = kChunkTargetMs / (double)ms;
+  f = f > 4.0 ? 4.0 : (f < 0.25 ? 0.25 : f);
+  int c = (int)floor(r->chunk * f + 0.5);
+  c = c < 1 ? 1 : (c > kMaxChunk ? kMaxChunk : c);
+  r->chunk = c;
 }
 
 int admit(ode_server* s, Pool& pl, Request* r) {
@@ -242,6 +283,7 @@ int admit(ode_server* s, Pool& pl, Request* r) {
   fill_int_kernel<<<(r->n + 255) / 256 < 1024 ? (r->n + 255) / 256 : 1024, 256, 0, st>>>(
       pl.left + r->off, r->n, r->periods);
   SCK(s, cudaGetLastError());
+  r->chunk = s->slice_periods > 0 ? s->slice_periods : 1;
   if (int rc = build_request_graph(s, pl, r)) return rc;
   r->state = kRunning;
   r->scheduled = 0;
@@ -277,7 +319,7 @@ extern "C" {
 int ode_server_create(ode_server** out, int device, long long hbm_budget_bytes, int slice_periods) {
   if (!out) return ODE_ERR_INVALID_ARG;
   *out = nullptr;
-  if (hbm_budget_bytes <= 0 || slice_periods < 1) return ODE_ERR_INVALID_ARG;
+  if (hbm_budget_bytes <= 0 || slice_periods < 0) return ODE_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ODE_ERR_CUDA;
   ode_server* s = new (std::nothrow) ode_server();
@@ -374,7 +416,7 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
 int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, const double* td,
                       const double* y0, const double* p, long long* ticket) {
   if (!s) return ODE_ERR_INVALID_ARG;
-  if (model < 0 || model > 3 || !s->pools[model].on)
+  if (model < 0 || model >= kNumModels || !s->pools[model].on)
     return sfail(s, ODE_ERR_INVALID_ARG, "model not served (ode_server_add_model)");
   Pool& pl = s->pools[model];
   if (n_systems < 1 || n_systems > pl.cap)
@@ -393,7 +435,10 @@ int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, co
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_status, n * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_acc_steps, n * sizeof(long long));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->chunk_ev, cudaEventDisableTiming);
+  // timing events only where the chunk length is tuned
+  const unsigned ev_flags = s->slice_periods == 0 ? cudaEventDefault : cudaEventDisableTiming;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->chunk_ev, ev_flags);
+  if (e == cudaSuccess && s->slice_periods == 0) e = cudaEventCreateWithFlags(&r->start_ev, ev_flags);
   if (e != cudaSuccess) {
     free_request(r);
     return scuda(s, e, "request buffers");
@@ -426,6 +471,7 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
         }
         if (q != cudaSuccess) return scuda(s, q, "chunk");
         r->chunk_inflight = false;
+        if (s->slice_periods == 0) retune_chunk(r);
       }
       if (r->scheduled >= r->periods) {
         if (int rc = harvest(s, pl, r)) return rc;

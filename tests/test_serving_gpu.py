@@ -41,6 +41,7 @@ def make_server(slice_periods=3):
     G.ode_server_add_model(srv, settings_for(W.duffing_rkck(1, 1, 0, 1)), 1e-2, 4096)
     G.ode_server_add_model(srv, settings_for(W.valve(1, 0, 1)), 1e-2, 4096)
     G.ode_server_add_model(srv, settings_for(W.keller_miksis(1, 1, 0, 1)), 1e-2, 4096)
+    G.ode_server_add_model(srv, settings_for(W.duffing_lyapunov(1, 0, 1)), 1e-2, 1024)
     return srv
 
 
@@ -120,3 +121,26 @@ def test_admission_waits_for_slots_and_rejects_oversized_requests():
             G.ode_server_add_model(srv, settings_for(W.valve(1, 0, 1)), 1e-2, 1 << 30)
     finally:
         G.ode_server_destroy(srv)
+
+
+def test_tuned_chunk_length_and_a_lyapunov_pool():
+    """Chunk length tuned per request (slice_periods = 0) gives the same
+    results as fixed chunks; the Lyapunov model is served like the others."""
+    wa, pa = request(W.DUFFING, 300, 9, seed=21)
+    wl = W.duffing_lyapunov(N=100, n_transient=4, n_record=1)
+    out = {}
+    for sp in (0, 2):
+        srv = make_server(slice_periods=sp)
+        try:
+            ta = G.ode_server_submit(srv, W.DUFFING, 9, wa["td"], wa["y0"], pa)
+            tl = G.ode_server_submit(srv, W.DUFFING_LYAPUNOV, 5, wl["td"], wl["y0"], wl["p"])
+            out[sp] = drain(srv, {ta: (W.DUFFING, 300), tl: (W.DUFFING_LYAPUNOV, 100)})
+            out[sp] = (out[sp][ta], out[sp][tl])
+        finally:
+            G.ode_server_destroy(srv)
+    for i in range(2):
+        for key in ("td", "y", "acc", "status", "nacc"):
+            np.testing.assert_array_equal(out[0][i][key], out[2][i][key], err_msg=key)
+    ref = run_gpu(wl, persistent=0)
+    np.testing.assert_array_equal(out[0][1]["y"], ref["y"])
+    np.testing.assert_array_equal(out[0][1]["acc"], ref["acc"])
