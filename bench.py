@@ -154,14 +154,14 @@ def rank_band(w, rank):
 
 
 def kernel_source_digest():
-    """sha256 over the integrator's CUDA sources and the ABI header: a DRAM
-    traffic figure measured by ncu applies only to the sources it was taken
-    on."""
+    """sha256 over the sources that define the integrator kernels (headers
+    and the per-model kernel units): a DRAM traffic figure measured by ncu
+    applies only to the kernel sources it was taken on."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1810_03931_gb300", "csrc")
-    files = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
-    for f in files + ["../../include/odegpu.h"]:
+    files = sorted(f for f in os.listdir(csrc) if f.endswith(".cuh") or f.startswith("kern_"))
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()
