@@ -667,7 +667,7 @@ struct Lane {
     steps++;
     if constexpr (SCHEME == kRKCK45) {
       // error ratio and step-size control (Sec. 3, Sec. 6.5)
-      // max_m |err_m| / sc_m with a single division: every ratio is brought
+      // max_m |err_m| / sc_m with a single reciprocal: every ratio is brought
       // over the common denominator prod_m sc_m.  Comparisons, maxima and
       // finiteness tests run on the integer pipe (all operands >= 0).
       double sc[n], num[n];
@@ -685,10 +685,10 @@ struct Lane {
       double nmax = num[0];
 #pragma unroll
       for (int m = 1; m < n; m++) nmax = dmax_nn(nmax, num[m]);  // NaN propagates
-      double errr = nmax / den;
-      if (!dpos(den) || !dfinite(den) || !dfinite(nmax)) {
-        // out of range for the common denominator (or NaN): one division
-        // per ratio, NaN kept
+      double errr = nmax * recip_nr(den);  // den normal and finite here (else below)
+      // den below the smallest normal double (the reciprocal flushes it),
+      // infinite, or NaN anywhere: one division per ratio, NaN kept
+      if (dbits(den) < dbits(2.2250738585072014e-308) || !dfinite(den) || !dfinite(nmax)) {
         errr = 0.0;
 #pragma unroll
         for (int m = 0; m < n; m++) {

@@ -46,6 +46,17 @@ __device__ __forceinline__ double rfifth_root(double x) {
   return z;
 }
 
+// 1 / x for finite, normal x: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64, about 2^-23 relative) refined by two Newton-Raphson
+// steps r <- r + r (1 - x r), each of which squares the relative error, to
+// within an ulp or two -- four FMAs instead of a correctly rounded division.
+__device__ __forceinline__ double recip_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 // rx^e with rx = 1 / x for the polytropic exponent e = 3 gamma.  When 5 e is a
 // small integer k (gamma = 1, 1.4 or 5/3 give k = 15, 21, 25) this is
 // rx^(k div 5) * (x^(-1/5))^(k mod 5): a few multiplications and one
@@ -142,7 +153,10 @@ struct KellerMiksis {
   static __device__ __forceinline__ void rhs(const Stage<T>& st, const T (&y)[N], const T (&C)[P],
                                              const T (&)[3], T (&f)[N]) {
     const double y1 = y[0], y2 = y[1];
-    const double rx = 1.0 / y1;
+    // both reciprocals (1 / y1 and 1 / den) from one: r = 1 / (y1 den)
+    const double den = y1 - C[9] * y1 * y2 + C[4] * C[9];
+    const double r = recip_nr(y1 * den);
+    const double rx = den * r;
     const double s1 = st.s, c1 = st.c;  // sin, cos of 2 pi tau
     double s2 = 0.0, c2 = 0.0;
     if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * st.t + C[12], &s2, &c2);
@@ -150,9 +164,8 @@ struct KellerMiksis {
     const double num = (C[0] + C[1] * y2) * polytropic_pow(y1, rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
                        C[4] * y2 * rx - (1.0 - C[9] * y2 * (1.0 / 3.0)) * 1.5 * y2 * y2 -
                        (C[5] * s1 + C[6] * s2) * one_c9y2 - y1 * (C[7] * c1 + C[8] * c2);
-    const double den = y1 - C[9] * y1 * y2 + C[4] * C[9];
     f[0] = y2;
-    f[1] = num / den;
+    f[1] = num * (y1 * r);
   }
   static __device__ __forceinline__ void events(double, const double (&y)[N], const double (&)[P],
                                                 double (&F)[E]) {
