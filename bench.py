@@ -643,8 +643,10 @@ def main():
                              "serving"])
     ap.add_argument("--requests", type=int, default=40, help="serving: requests per run")
     ap.add_argument("--slice-periods", type=int, default=2, help="serving: periods per tick")
-    ap.add_argument("--max-log2-size", type=int, default=16, help="serving: sizes floor(2^U(0, x))")
-    ap.add_argument("--max-log2-horizon", type=int, default=10, help="serving: horizons floor(2^U(4, x))")
+    # the full mix (sizes to 2^16, horizons to 1024 periods) takes about an
+    # hour per pass; the default is a bounded mix that keeps the run to minutes
+    ap.add_argument("--max-log2-size", type=int, default=14, help="serving: sizes floor(2^U(0, x))")
+    ap.add_argument("--max-log2-horizon", type=int, default=8, help="serving: horizons floor(2^U(4, x))")
     ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 1.0])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32rhs"])
     ap.add_argument("--persistent", type=int, default=1)
