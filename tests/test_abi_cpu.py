@@ -128,3 +128,19 @@ def test_cluster_order_is_a_z_order_permutation():
     assert step(cl) < 0.1 * step(sh)
     with pytest.raises(G.ODEError):
         G.ode_cluster_order(np.zeros((9, 4)))
+
+
+def test_bench_uses_a_measured_traffic_only_for_its_kernel_sources(tmp_path):
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    path = str(tmp_path / "t.json")
+    entry = {"per_sweep": {"source_sha256": bench.kernel_source_digest(), "dram_bytes_per_launch": 1.5e9}}
+    json.dump({"duffing_rkck_512x256": entry}, open(path, "w"))
+    assert bench.measured_traffic("duffing_rkck_512x256", 0, path) == 1.5e9
+    assert bench.measured_traffic("duffing_rkck_512x256", 1, path) is None  # other launch form
+    assert bench.measured_traffic("valve_65536", 0, path) is None
+    entry["per_sweep"]["source_sha256"] = "0" * 64  # taken on other sources
+    json.dump({"duffing_rkck_512x256": entry}, open(path, "w"))
+    assert bench.measured_traffic("duffing_rkck_512x256", 0, path) is None
