@@ -171,7 +171,7 @@ def measured_traffic(workload_name, launch, path=None):
     """DRAM bytes (read + write) of one integrator launch of this workload
     and launch form, from the ncu summary committed under profiles/ -- or None
     when it was taken on other kernel sources."""
-    path = path or os.path.join(ROOT, "profiles", "dram_traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
