@@ -65,6 +65,7 @@ class _Trace(ctypes.Structure):
         ("ev_index", ctypes.POINTER(ctypes.c_int)),
         ("ev_t", ctypes.POINTER(ctypes.c_double)),
         ("ev_y", ctypes.POINTER(ctypes.c_double)),
+        ("ev_y_after", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -249,13 +250,16 @@ def trace_slice(cfg: Config, td, y, p, acc=None, cap=1_000_000, ev_cap=100_000):
     ev_index = np.zeros(ev_cap, dtype=np.int32)
     ev_t = np.zeros(ev_cap)
     ev_y = np.zeros((ev_cap, MAXN))
-    tr = _Trace(cap, 0, _dp(tbuf), _dp(ybuf), ev_cap, 0, _ip(ev_index), _dp(ev_t), _dp(ev_y))
+    ev_y_after = np.zeros((ev_cap, MAXN))
+    tr = _Trace(cap, 0, _dp(tbuf), _dp(ybuf), ev_cap, 0, _ip(ev_index), _dp(ev_t), _dp(ev_y),
+                _dp(ev_y_after))
     st = lib().orc_trace_slice(ctypes.byref(cfg), _dp(td), _dp(y), _dp(p), _dp(acc), _ip(ecnt),
                                _lp(nacc), _lp(nrej), ctypes.byref(tr))
     k, m = tr.n_points, tr.n_events
     return dict(status=st, td=td, y=y, acc=acc, ecnt=ecnt[:E].copy(), nacc=int(nacc[0]),
                 nrej=int(nrej[0]), t=tbuf[:k].copy(), ys=ybuf[:k, :n].copy(),
-                ev_index=ev_index[:m].copy(), ev_t=ev_t[:m].copy(), ev_y=ev_y[:m, :n].copy())
+                ev_index=ev_index[:m].copy(), ev_t=ev_t[:m].copy(), ev_y=ev_y[:m, :n].copy(),
+                ev_y_after=ev_y_after[:m, :n].copy())
 
 
 def single_step(cfg: Config, t, y, p, h):

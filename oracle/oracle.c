@@ -99,6 +99,7 @@ typedef struct orc_trace {
     int *ev_index;     /* [ev_cap] */
     double *ev_t;      /* [ev_cap] */
     double *ev_y;      /* [ev_cap * ORC_MAXN], state before the action */
+    double *ev_y_after; /* [ev_cap * ORC_MAXN], state after it (may be NULL) */
 } orc_trace;
 
 /* ------------------------------------------------------------------------ */
@@ -552,6 +553,9 @@ static int integrate_slice(const orc_config *c, int n, int A, int E,
                 }
                 acc_event(c, j, ecnt[j], t, y, a);
                 event_action(c, j, y, p);
+                if (tr && tr->ev_y_after && tr->n_events > 0 && tr->n_events <= tr->ev_cap)
+                    for (int m = 0; m < n; m++)
+                        tr->ev_y_after[(tr->n_events - 1) * ORC_MAXN + m] = y[m];
             }
             /* Zone bookkeeping at the (post-action) accepted point. */
             event_functions(c, t, y, p, F);

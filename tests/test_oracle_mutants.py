@@ -34,6 +34,12 @@ MUTANTS = [
      "C[8] = RE * omega1 * PA2 / (rho * cL) * s2;", [P.test_km_dual_frequency_matches_dimensional]),
     ("valve_sqrt", "q - y[0] * sqrt(y[2])", "q - y[0] * y[2]",
      [P.test_valve_high_flow_rate_settles_to_equilibrium]),
+    ("valve_restitution", "y[1] = -p[4] * y[1];", "y[1] = -p[3] * y[1];", [P.test_valve_impact_law]),
+    ("km_polytropic_exponent", "C[10] = 3.0 * gamma;", "C[10] = 3.0;",
+     [lambda: P.test_km_dimensionless_matches_dimensional(1.2e5, 300e3)]),
+    ("km_liquid_compressibility", "C[1] = (1.0 - 3.0 * gamma) / (rho * cL) * Pg0 * s;",
+     "C[1] = (1.0 - 3.0 * gamma) / rho * Pg0 * s;",
+     [lambda: P.test_km_dimensionless_matches_dimensional(1.2e5, 300e3)]),
     ("accessory_min", "if (y[0] < a[2]) { a[2] = y[0]; a[3] = t; }", "if (y[0] > a[2]) { a[2] = y[0]; a[3] = t; }",
      [P.test_accessories_equal_brute_force_over_accepted_points]),
     ("zone_at_start", "leaving[j] = fabs(F[j]) <= c->evt_tol[j];", "leaving[j] = 0;",

@@ -608,6 +608,24 @@ def test_valve_high_flow_rate_settles_to_equilibrium():
     assert abs(r["acc"][0, 0] - r["acc"][2, 0]) < 1e-3
 
 
+def test_valve_impact_law():
+    """Eqs. (32)-(34) at every located impact: y1 stays at the seat (within
+    the event tolerance), y2+ = -r y2-, y3 is continuous."""
+    r_coef = GOLD["valve"]["r"]
+    cfg = _valve_cfg()
+    p = np.array(_valve_params(2.0))
+    first = O.run(cfg, [[0.0], [1e3]], [[0.2], [0.0], [10.0]], p)  # up to the first maximum
+    tr = O.trace_slice(cfg, first["td"][:, 0], first["y"][:, 0], p[:, 0])  # falls onto the seat
+    imp = tr["ev_index"] == 1
+    assert imp.sum() >= 1
+    before, after = tr["ev_y"][imp], tr["ev_y_after"][imp]
+    assert np.all(before[:, 1] < 0)
+    np.testing.assert_array_equal(after[:, 1], -r_coef * before[:, 1])
+    np.testing.assert_array_equal(after[:, 0], before[:, 0])
+    np.testing.assert_array_equal(after[:, 2], before[:, 2])
+    assert np.all(np.abs(before[:, 0]) <= cfg.evt_tol[1])
+
+
 def test_valve_low_flow_rate_impacts():
     r = O.run(_valve_cfg(), [[0.0], [1e3]], [[0.2], [0.0], [10.0]], _valve_params(2.0), n_slices=40,
               n_skip=20, record=True)
