@@ -10,7 +10,8 @@ one whole pass: reset the initial conditions from HBM, integrate every system
 over all 1088 periods in one persistent launch, write the 64 records.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       [--workload duffing_rkck|duffing_rk4|valve|keller_miksis|duffing_lyapunov]
+       [--workload duffing_rkck|duffing_rk4|valve|keller_miksis|duffing_lyapunov|
+                   keller_miksis_collapse|keller_miksis_dual|valve_paper|serving]
 Under torchrun each rank integrates its own sweep (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
@@ -45,7 +46,8 @@ import workloads as W  # noqa: E402
 # linearisation (n = 4): 6 x 23 + 10 + 140 + 36 + 40 + 20 + 20 + 1 = 405
 # (+ 6 cos of the forcing, 6 sincos of the angle, credited as cos).
 FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_miksis": 365,
-                  "duffing_lyapunov": 405}
+                  "duffing_lyapunov": 405, "keller_miksis_collapse": 365, "keller_miksis_dual": 365,
+                  "valve_paper": 274}
 # The binary32 right-hand-side form splits those flops: binary64 keeps the
 # update (1 fma per component), the error estimate (1 mul per component), the
 # error norm, the controller and the time update; the rest (right-hand sides,
@@ -55,8 +57,12 @@ FLOPS_PER_STEP = {"duffing_rkck": 209, "duffing_rk4": 77, "valve": 274, "keller_
 FLOPS_FP32RHS = {"duffing_rkck": (37, 172), "valve": (45, 229)}
 # transcendental calls per accepted step, converted to DFMA equivalents with
 # the library's call-cost probe (one DFMA = 2 flops) for the FMA-peak roofline
+# (the dual-frequency Keller-Miksis adds sin and cos of the second drive per
+# stage: 12 more)
 TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {},
-                   "keller_miksis": {"pow": 6, "cos": 12}, "duffing_lyapunov": {"cos": 12}}
+                   "keller_miksis": {"pow": 6, "cos": 12}, "duffing_lyapunov": {"cos": 12},
+                   "keller_miksis_collapse": {"pow": 6, "cos": 12},
+                   "keller_miksis_dual": {"pow": 6, "cos": 24}, "valve_paper": {}}
 METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
 METRIC_FP32RHS = "accepted system-steps/s (binary32 RHS stages, binary64 state and control, rtol 1e-10)"
 UNIT = "system-steps/s"
@@ -73,6 +79,14 @@ def workload(name, rank=0):
         return W.keller_miksis(n_transient=16, n_record=16)
     if name == "duffing_lyapunov":
         return W.duffing_lyapunov()
+    # the paper's own protocols (Sec. 7.2, 7.3), bounded to a few seconds per
+    # pass: collapse-to-collapse iterations (16 + 8 instead of 1024 + 64)
+    if name == "keller_miksis_collapse":
+        return W.keller_miksis_collapse(255, 256, n_transient=16, n_record=8)
+    if name == "keller_miksis_dual":
+        return W.keller_miksis_dual(128, 128, n_transient=16, n_record=8)
+    if name == "valve_paper":
+        return dict(W.valve(rtol=1e-10), name="valve_65536_rtol1e-10")
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -83,7 +97,9 @@ def describe(w, persistent, l2):
                     2: "persistent work queue (lane order)"}[persistent],
          "l2": l2}
     if w["events_on"]:
-        d["events"] = "y2=0 dir -1 located to %g" % w["evt_tol"][0] if w["model"] == 0 else "2 events"
+        d["events"] = ("y2=0 (maximum, stop 1) and y1=0 (impact, y2 <- -r y2), tol %g" % w["evt_tol"][0]
+                       if w["model"] == W.VALVE else
+                       "y2=0 dir %d located to %g, stop %d" % (w["evt_dir"][0], w["evt_tol"][0], w["evt_stop"][0]))
     return d
 
 
@@ -640,7 +656,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="duffing_rkck",
                     choices=["duffing_rkck", "duffing_rk4", "valve", "keller_miksis", "duffing_lyapunov",
-                             "serving"])
+                             "keller_miksis_collapse", "keller_miksis_dual", "valve_paper", "serving"])
     ap.add_argument("--requests", type=int, default=40, help="serving: requests per run")
     ap.add_argument("--slice-periods", type=int, default=2, help="serving: periods per tick")
     # the full mix (sizes to 2^16, horizons to 1024 periods) takes about an
