@@ -246,6 +246,27 @@ def test_keller_miksis_collapse_protocols(make):
     _compare_records(g, o, mask, 4, 2, tol=tol)
 
 
+@pytest.mark.parametrize("make,block", [
+    (lambda: W.keller_miksis_collapse(255, 256, n_transient=16, n_record=8), 256),
+    (lambda: W.keller_miksis_dual(128, 128, n_transient=16, n_record=8), 64)],
+    ids=["collapse_iteration_65280", "dual_frequency_table5_65536"])
+def test_keller_miksis_protocols_bench_size_sampled(make, block):
+    """The collapse and dual-frequency protocols at the benchmark's sizes and
+    launch shape; sampled systems (grid corners included) replayed one by one
+    by the oracle and compared on well-conditioned points at 100 x the event
+    tolerance."""
+    w = make()
+    g = run_gpu(w, persistent=0, block=block)
+    assert np.all(g["status"] == G.ODE_ST_EVENT_STOP)
+    idx = W.sample_indices(w["N"], 40, corners=(0, 255, w["N"] - 256, w["N"] - 1))
+    ws = W.subset(w, idx)
+    tol = 100 * w["evt_tol"][0]
+    mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 6), rtol=1e-10, agree=tol)
+    gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+    assert mask.sum() >= 10
+    _compare_records(gs, o, mask, 4, 2, tol=tol)
+
+
 # ---------------------------------------------------------------------------
 # Pressure relief valve with two events, impact action and equilibrium stop
 # (Sec. 7.3), per-sweep and persistent launches.
