@@ -124,9 +124,10 @@ def test_duffing_rkck_event_parity_grid():
 
 def test_duffing_rkck_full_size_sampled():
     """The bench workload at full size (2^17 systems, 1024 + 64 periods), in the
-    bench's launch form; sampled systems replayed one by one by the oracle."""
+    launch form the bench's autotuner picks; sampled systems replayed one by one
+    by the oracle."""
     w = W.duffing_rkck()
-    g = run_gpu(w, persistent=1)
+    g = run_gpu(w, autotune=True)
     assert np.all(np.isin(g["status"], [1]))
     idx = W.sample_indices(w["N"], 40, corners=(0, 511, w["N"] - 512, w["N"] - 1))
     ws = W.subset(w, idx)
@@ -186,7 +187,7 @@ def test_duffing_lyapunov_full_size_sampled():
     rtol and at rtol / 10 differs there by ~1e-6.  Those two rows are held to
     10 x that spread; the oscillator's own state and extrema to 100 x rtol."""
     w = W.duffing_lyapunov()
-    g = run_gpu(w, persistent=1)
+    g = run_gpu(w, autotune=True)
     assert np.all(g["status"] == 1)
     idx = W.sample_indices(w["N"], 32, corners=(0, 1, w["N"] - 2, w["N"] - 1))
     ws = W.subset(w, idx)
@@ -246,17 +247,17 @@ def test_keller_miksis_collapse_protocols(make):
     _compare_records(g, o, mask, 4, 2, tol=tol)
 
 
-@pytest.mark.parametrize("make,block", [
-    (lambda: W.keller_miksis_collapse(255, 256, n_transient=16, n_record=8), 256),
-    (lambda: W.keller_miksis_dual(128, 128, n_transient=16, n_record=8), 64)],
+@pytest.mark.parametrize("make", [
+    lambda: W.keller_miksis_collapse(255, 256, n_transient=16, n_record=8),
+    lambda: W.keller_miksis_dual(128, 128, n_transient=16, n_record=8)],
     ids=["collapse_iteration_65280", "dual_frequency_table5_65536"])
-def test_keller_miksis_protocols_bench_size_sampled(make, block):
-    """The collapse and dual-frequency protocols at the benchmark's sizes and
-    launch shape; sampled systems (grid corners included) replayed one by one
+def test_keller_miksis_protocols_bench_size_sampled(make):
+    """The collapse and dual-frequency protocols at the benchmark's sizes in the
+    autotuned launch shape; sampled systems (grid corners included) replayed one by one
     by the oracle and compared on well-conditioned points at 100 x the event
     tolerance."""
     w = make()
-    g = run_gpu(w, persistent=0, block=block)
+    g = run_gpu(w, autotune=True)
     assert np.all(g["status"] == G.ODE_ST_EVENT_STOP)
     idx = W.sample_indices(w["N"], 40, corners=(0, 255, w["N"] - 256, w["N"] - 1))
     ws = W.subset(w, idx)
