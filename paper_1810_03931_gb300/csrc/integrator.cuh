@@ -121,16 +121,13 @@ __device__ __forceinline__ void sincos_quarter(double a, float& s, float& c) {
   const int q = __double2loint(ks) & 3;
   const float r = (float)fma(-(ks - kShift), 0.5 * CUDART_PI, a);
   const float r2 = r * r;
-  const float sr =
-      r * fmaf(fmaf(fmaf(fmaf(r2, (float)sin_coef(1.0, 4), (float)sin_coef(1.0, 3)), r2,
-                          (float)sin_coef(1.0, 2)),
-                     r2, (float)sin_coef(1.0, 1)),
-                r2, 1.0f);
-  const float cr = fmaf(fmaf(fmaf(fmaf(fmaf(r2, (float)cos_coef(1.0, 5), (float)cos_coef(1.0, 4)), r2,
-                                       (float)cos_coef(1.0, 3)),
-                                  r2, (float)cos_coef(1.0, 2)),
-                             r2, (float)cos_coef(1.0, 1)),
-                        r2, 1.0f);
+  // coefficients as compile-time constants
+  constexpr float s1 = (float)sin_coef(1.0, 1), s2 = (float)sin_coef(1.0, 2), s3 = (float)sin_coef(1.0, 3),
+                  s4 = (float)sin_coef(1.0, 4);
+  constexpr float c1 = (float)cos_coef(1.0, 1), c2 = (float)cos_coef(1.0, 2), c3 = (float)cos_coef(1.0, 3),
+                  c4 = (float)cos_coef(1.0, 4), c5 = (float)cos_coef(1.0, 5);
+  const float sr = r * fmaf(fmaf(fmaf(fmaf(r2, s4, s3), r2, s2), r2, s1), r2, 1.0f);
+  const float cr = fmaf(fmaf(fmaf(fmaf(fmaf(r2, c5, c4), r2, c3), r2, c2), r2, c1), r2, 1.0f);
   const float ns = -sr, nc = -cr;
   s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? ns : nc;
   c = (q == 0) ? cr : (q == 1) ? ns : (q == 2) ? nc : sr;
@@ -141,8 +138,10 @@ __device__ __forceinline__ void sincos_quarter(double a, float& s, float& c) {
 template <int CNUM, int CDEN>
 __device__ __forceinline__ void small_angle_f(float x, float U, float& cd, float& sd) {
   constexpr double c = (double)CNUM / (double)CDEN;
-  cd = fmaf(fmaf(U, (float)cos_coef(c, 2), (float)cos_coef(c, 1)), U, 1.0f);
-  sd = x * fmaf(fmaf(U, (float)sin_coef(c, 2), (float)sin_coef(c, 1)), U, (float)sin_coef(c, 0));
+  constexpr float a1 = (float)cos_coef(c, 1), a2 = (float)cos_coef(c, 2);
+  constexpr float b0 = (float)sin_coef(c, 0), b1 = (float)sin_coef(c, 1), b2 = (float)sin_coef(c, 2);
+  cd = fmaf(fmaf(U, a2, a1), U, 1.0f);
+  sd = x * fmaf(fmaf(U, b2, b1), U, b0);
 }
 
 // ---- one trial step --------------------------------------------------------
@@ -204,14 +203,12 @@ struct Stepper {
     return st;
   }
 
-  static __device__ __forceinline__ void step(double t, const double (&y)[n], double hs,
-                                              const T (&pt)[P], const T (&mct)[3],
+  // yb: the state y in precision T (y itself in binary64)
+  static __device__ __forceinline__ void step(double t, const double (&y)[n], const T (&yb)[n],
+                                              double hs, const T (&pt)[P], const T (&mct)[3],
                                               const T (&k1)[n], T C, T S, double w,
                                               double (&ynew)[n], double (&err)[n], double& Cn,
                                               double& Sn) {
-    T yb[n];
-#pragma unroll
-    for (int m = 0; m < n; m++) yb[m] = (T)y[m];
     const T h = (T)hs;
     const T tb = (T)t;
     const double x = w * hs, U = x * x;
@@ -372,6 +369,7 @@ struct Lane {
   double fC, fS;    // cos, sin of omega t at the lane's t (binary64 forcing)
   double fCn, fSn;  // the same at t + hs of the last normal trial step
   T gC, gS;         // binary32 form: cos, sin of omega t at the lane's t
+  T yt[n];          // binary32 form: the state y rounded once per accepted point
   double w;         // forcing angular frequency
 
   // Load the slot; false when the system has no slice to run in this launch.
@@ -604,9 +602,11 @@ struct Lane {
       }
     }
     if (!k1ok) {
-      T yb[n];
+      if constexpr (PREC != kFP64) {
+        // the state in binary32, kept for the trials from this point
 #pragma unroll
-      for (int m = 0; m < n; m++) yb[m] = (T)y[m];
+        for (int m = 0; m < n; m++) yt[m] = (T)y[m];
+      }
       Stage<T> st0;
       if constexpr (St::kRotate) {
         st0.t = t;
@@ -620,12 +620,14 @@ struct Lane {
         st0.c = gC;
         st0.s = gS;
       }
-      M::template rhs<T>(st0, yb, pt, mct, k1);
+      if constexpr (PREC == kFP64) M::template rhs<T>(st0, y, pt, mct, k1);
+      else M::template rhs<T>(st0, yt, pt, mct, k1);
       k1ok = true;
     }
     double ynew[n], err[n], Cn = 0.0, Sn = 0.0;
-    if constexpr (St::kRotate) St::step(t, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
-    else St::step(t, y, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
+    if constexpr (St::kRotate) St::step(t, y, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
+    else if constexpr (PREC == kFP64) St::step(t, y, y, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
+    else St::step(t, y, yt, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
     if (!locating) {
       fCn = Cn;
       fSn = Sn;
