@@ -59,10 +59,10 @@ FLOPS_FP32RHS = {"duffing_rkck": (37, 172), "valve": (45, 229)}
 # the library's call-cost probe (one DFMA = 2 flops) for the FMA-peak roofline
 # (the dual-frequency Keller-Miksis adds sin and cos of the second drive per
 # stage: 12 more)
-TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {},
+TRANSCENDENTALS = {"duffing_rkck": {"cos": 6}, "duffing_rk4": {"cos": 4}, "valve": {"sqrt": 6},
                    "keller_miksis": {"pow": 6, "cos": 12}, "duffing_lyapunov": {"cos": 12},
                    "keller_miksis_collapse": {"pow": 6, "cos": 12},
-                   "keller_miksis_dual": {"pow": 6, "cos": 24}, "valve_paper": {}}
+                   "keller_miksis_dual": {"pow": 6, "cos": 24}, "valve_paper": {"sqrt": 6}}
 METRIC = "accepted system-steps/s (FP64, rtol 1e-10)"
 METRIC_FP32RHS = "accepted system-steps/s (binary32 RHS stages, binary64 state and control, rtol 1e-10)"
 UNIT = "system-steps/s"
@@ -365,12 +365,12 @@ def run_gpu(args):
     if not max_mhz:
         max_mhz = clk.get("sm_max_mhz") or 2070.0
     dfma, ffma = G.ode_probe_fma_peak(local)
-    cos_eq, pow_eq = G.ode_probe_call_cost(local)
+    cos_eq, pow_eq, sqrt_eq = G.ode_probe_call_cost(local)
     peak_tflops = 2 * 2 * sms * max_mhz * 1e6 / 1e12
     peak32_tflops = 128 * 2 * sms * max_mhz * 1e6 / 1e12  # 128 binary32 FMA lanes per SM
     arith = FLOPS_PER_STEP.get(args.workload, 0)
     trans = TRANSCENDENTALS.get(args.workload, {})
-    eq = {"cos": cos_eq, "pow": pow_eq}
+    eq = {"cos": cos_eq, "pow": pow_eq, "sqrt": sqrt_eq}
     per_step = arith + sum(2.0 * eq[k] * v for k, v in trans.items())
     fp32_split = None
     if args.prec == "fp32rhs":
@@ -414,7 +414,8 @@ def run_gpu(args):
                                        % (sms, max_mhz, 2 * dfma / 1e12),
                          "flops_per_step": per_step, "arith_flops_per_step": arith,
                          "transcendentals_per_step": trans,
-                         "call_cost_dfma_equiv": {"cos": round(cos_eq, 2), "pow": round(pow_eq, 2)},
+                         "call_cost_dfma_equiv": {"cos": round(cos_eq, 2), "pow": round(pow_eq, 2),
+                                                  "sqrt": round(sqrt_eq, 2)},
                          "achieved_arith_only": achieved_arith, "frac_arith_only": achieved_arith / peak_tflops},
             # accepted steps differ between forms (the binary32 error estimate
             # carries rounding noise): system-periods/s compares them on work

@@ -298,11 +298,11 @@ int ode_kernel_info(int model, int scheme, int prec, int persistent, int block_s
  * the roofline peak of the arithmetic-bound integrators. */
 int ode_probe_fma_peak(int device, double *dfma_per_s, double *ffma_per_s);
 
-/* Measured cost of one binary64 cos() and one pow() call, in DFMA
+/* Measured cost of one binary64 cos(), pow() and sqrt() call, in DFMA
  * equivalents (call throughput relative to the DFMA issue rate, with the loop
  * overhead subtracted).  Used to count the transcendental calls of an
- * algorithm in the FMA-peak roofline. */
-int ode_probe_call_cost(int device, double *cos_dfma, double *pow_dfma);
+ * algorithm in the FMA-peak roofline.  Any output may be NULL. */
+int ode_probe_call_cost(int device, double *cos_dfma, double *pow_dfma, double *sqrt_dfma);
 
 /* Settings of ode_run_periods_noalloc (host memory, read during the call).
  * rtol / atol: first n entries used; direction / tolerance / stop_count:

@@ -47,7 +47,7 @@ cudaError_t time_chains(int sms, int iters, double* fma_per_s) {
   return e;
 }
 
-// Cost of a binary64 cos (and of a general pow) in units of the DFMA issue
+// Cost of a binary64 cos, a general pow and a sqrt in units of the DFMA issue
 // rate: four independent accumulation chains per thread with and without the
 // call; the difference isolates the call.
 template <int KIND>
@@ -59,6 +59,8 @@ __global__ void call_chains(double* out, int iters) {
       s0 += cos(x0); s1 += cos(x1); s2 += cos(x2); s3 += cos(x3);
     } else if (KIND == 2) {
       s0 += pow(x0, -0.2); s1 += pow(x1, -0.2); s2 += pow(x2, -0.2); s3 += pow(x3, -0.2);
+    } else if (KIND == 3) {
+      s0 += sqrt(x0); s1 += sqrt(x1); s2 += sqrt(x2); s3 += sqrt(x3);
     } else {
       s0 += x0; s1 += x1; s2 += x2; s3 += x3;
     }
@@ -97,21 +99,23 @@ cudaError_t time_calls(int sms, int iters, double* seconds) {
 
 }  // namespace
 
-extern "C" int ode_probe_call_cost(int device, double* cos_dfma, double* pow_dfma) {
+extern "C" int ode_probe_call_cost(int device, double* cos_dfma, double* pow_dfma, double* sqrt_dfma) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (cudaSetDevice(device) != cudaSuccess) return ODE_ERR_CUDA;
   int sms = 0;
-  double dfma = 0, t_cos = 0, t_pow = 0, t_loop = 0;
+  double dfma = 0, t_cos = 0, t_pow = 0, t_sqrt = 0, t_loop = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = time_chains<double>(sms, 1000, &dfma);
   if (e == cudaSuccess) e = time_calls<1>(sms, 2000, &t_cos);
   if (e == cudaSuccess) e = time_calls<2>(sms, 500, &t_pow);
+  if (e == cudaSuccess) e = time_calls<3>(sms, 2000, &t_sqrt);
   if (e == cudaSuccess) e = time_calls<0>(sms, 2000, &t_loop);
   // GPU seconds per call (all threads together) x DFMA per second of the GPU
   if (e == cudaSuccess) {
     if (cos_dfma) *cos_dfma = (t_cos - t_loop) * dfma;
     if (pow_dfma) *pow_dfma = (t_pow - t_loop) * dfma;
+    if (sqrt_dfma) *sqrt_dfma = (t_sqrt - t_loop) * dfma;
   }
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   return e == cudaSuccess ? ODE_OK : ODE_ERR_CUDA;

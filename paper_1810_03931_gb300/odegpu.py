@@ -109,7 +109,7 @@ def load(build_if_missing: bool = True):
         "ode_cluster_order": [_dp, i, i, _ip],
         "ode_kernel_info": [i, i, i, i, i, i, _ip, _ip, _ip],
         "ode_probe_fma_peak": [i, _dp, _dp],
-        "ode_probe_call_cost": [i, _dp, _dp],
+        "ode_probe_call_cost": [i, _dp, _dp, _dp],
         "ode_run_periods_noalloc": [ctypes.POINTER(NoAllocSettings), i, i, d, i, i, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_char_p)],
     }
@@ -336,9 +336,10 @@ def ode_kernel_info(model, scheme, prec, persistent=0, block_size=0, device=0):
 
 
 def ode_probe_call_cost(device=0):
-    c, p = ctypes.c_double(), ctypes.c_double()
-    _check(load().ode_probe_call_cost(device, ctypes.byref(c), ctypes.byref(p)))
-    return c.value, p.value
+    """(cos, pow, sqrt) cost in DFMA equivalents."""
+    c, p, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().ode_probe_call_cost(device, ctypes.byref(c), ctypes.byref(p), ctypes.byref(q)))
+    return c.value, p.value, q.value
 
 
 def ode_probe_fma_peak(device=0):
