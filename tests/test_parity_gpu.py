@@ -467,6 +467,25 @@ def test_fp32_rhs_forcing_phase_at_large_t():
     assert err < 1e-5
 
 
+def test_fp32_rhs_full_size_sampled_report():
+    """The binary32 form of the bench sweep at full size (2^17 systems, 1024 + 64
+    periods): the error of sampled systems against the binary64 oracle is
+    reported per quantity (no tolerance is claimed); a bound far above it
+    guards against a broken form."""
+    w = W.duffing_rkck()
+    g = run_gpu(w, prec=G.ODE_FP32_RHS, autotune=True)
+    assert np.all(g["status"] == 1)
+    idx = W.sample_indices(w["N"], 32, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    ws = W.subset(w, idx)
+    mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
+    rg, ro = g["records"][:, :, idx][:, :, mask], o["records"][:, :, mask]
+    err = {name: float(np.max(np.abs(rg[:, row] - ro[:, row])))
+           for name, row in (("event y1", 4), ("event t", 5), ("end y1", 7), ("end y2", 8))}
+    print("FP32_RHS full size, %d of %d sampled points well-conditioned: %s" % (
+        mask.sum(), len(idx), ", ".join("%s %.2e" % kv for kv in err.items())))
+    assert mask.sum() >= 10 and max(err.values()) < 1e-3
+
+
 # ---------------------------------------------------------------------------
 # Edge cases: partial warps / blocks, a single system, empty and ragged time
 # domains, NaN parameters, step budget.
