@@ -53,6 +53,11 @@ MUTANTS = [
      [lambda: P.test_lyapunov_nonlinear_against_cartesian_tangent_flow(-1.0)]),
     ("lyap_radius_not_reset", "        y[2] = 1.0;\n", "",
      [P.test_lyapunov_linear_oscillator_matches_matrix_exponential]),
+    ("lyap_printed_mean_of_y3", "a[4] = log(y[2]);", "a[4] = y[2];",
+     [P.test_lyapunov_linear_oscillator_matches_matrix_exponential,
+      P.test_lyapunov_linear_oscillator_exponent_is_minus_half_damping]),
+    ("rk4_stage_time", "RK4_C[4] = {0.0, 0.5, 0.5, 1.0};", "RK4_C[4] = {0.0, 0.5, 0.5, 0.5};",
+     [P.test_linear_oscillator_rk4_error_bound]),
 ]
 
 
