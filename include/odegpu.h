@@ -379,8 +379,6 @@ const char *ode_server_last_error(const ode_server *s);
 
 /* ---- integration without allocation ---------------------------------------- */
 
-
-
 /* The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory themselves or through the library: code whose
  * device memory is owned by another allocator's pool (a framework caching
@@ -397,8 +395,12 @@ const char *ode_server_last_error(const ode_server *s);
  * kernel's other global memory (work-queue head, watchdog flag, per-system
  * stop status, event counters and step counters) is a fixed array inside the
  * library, reserved on every GPU that loads the library's device code and
- * kept until the process exits; it holds at most 65536 systems, and larger
- * n_systems are rejected with ODE_ERR_INVALID_ARG.  status [N] (int) and
+ * kept until the process exits (1 835 264 bytes: a 256-byte header, then the
+ * step counters, the status and the event counters, each section starting on
+ * a 256-byte boundary so that every one is aligned for its type whatever
+ * n_systems is); it holds at most 65536 systems, and larger n_systems are
+ * rejected with ODE_ERR_INVALID_ARG, as are arrays not aligned for their
+ * element type.  status [N] (int) and
  * accepted [N] (long long), device arrays or NULL, receive the stop status
  * and the accepted-step count of this call.
  *

@@ -13,21 +13,22 @@
 // loaded on a GPU and kept until the process exits.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <mutex>
 
 #include "../../include/odegpu.h"
 #include "common.cuh"
+#include "noalloc_layout.h"
 
 using namespace odegpu;
 
 namespace {
 
 constexpr int kNoAllocMaxSystems = 65536;
-constexpr size_t kHeadBytes = 256;  // queue head at 0, watchdog flag at 64
-constexpr size_t kPerSystemBytes = sizeof(int) + kMaxE * sizeof(int) + 2 * sizeof(long long);
-constexpr size_t kScratchBytes = kHeadBytes + (size_t)kNoAllocMaxSystems * kPerSystemBytes;
+// sections on 256-byte boundaries (noalloc_layout.h): 1 835 264 bytes
+constexpr size_t kScratchBytes = noalloc_layout(kNoAllocMaxSystems, kMaxE).total;
 
 // Device scratch shared by every call on a device.  In host code this name is
 // a host-side stand-in, not a device address: the address comes from
@@ -95,6 +96,11 @@ extern "C" int ode_run_periods_noalloc(const ode_noalloc_settings* cfg, int n_sy
   if (n_transient < 0 || n_record < 0 || (long long)n_transient + n_record > 0x7fffffffLL)
     return bad("bad slice counts");
   if (!td || !y || !p || !acc) return bad("td, y, p and acc are required device arrays");
+  if ((uintptr_t)td % alignof(double) || (uintptr_t)y % alignof(double) ||
+      (uintptr_t)p % alignof(double) || (uintptr_t)acc % alignof(double) ||
+      (uintptr_t)records % alignof(double) || (uintptr_t)status % alignof(int) ||
+      (uintptr_t)accepted % alignof(long long))
+    return bad("an array is not aligned for its element type");
   if (!(cfg->h_min > 0.0) || !(cfg->h_max >= cfg->h_min) || !isfinite(cfg->h_max) ||
       !(cfg->grow_limit >= 1.0) || !(cfg->grow_limit <= 1e4) || !(cfg->shrink_limit >= 1e-4) ||
       !(cfg->shrink_limit <= 1.0))
@@ -138,14 +144,20 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   if ((e = scratch_address(device, &scratch)) != cudaSuccess) return cuda_bad(e);
 
   const size_t N = (size_t)n_systems;
-  unsigned char* q = scratch + kHeadBytes;
-  int* d_status = (int*)q;
-  int* d_ecnt = (int*)(q + N * sizeof(int));
-  long long* d_nacc = (long long*)(q + N * (sizeof(int) + kMaxE * sizeof(int)));
-  long long* d_nrej = d_nacc + N;
+  const NoAllocLayout lay = noalloc_layout(N, kMaxE);
+  if (lay.total > kScratchBytes) return bad("scratch layout exceeds the fixed array");
+  long long* d_nacc = (long long*)(scratch + lay.nacc);
+  long long* d_nrej = (long long*)(scratch + lay.nrej);
+  int* d_status = (int*)(scratch + lay.status);
+  int* d_ecnt = (int*)(scratch + lay.ecnt);
+  // every section must be aligned for its element type before the kernel
+  // touches it (a misaligned 8-byte access is a device fault)
+  if ((uintptr_t)scratch % kNoAllocAlign != 0 || (uintptr_t)d_nacc % alignof(long long) != 0 ||
+      (uintptr_t)d_nrej % alignof(long long) != 0 || (uintptr_t)d_status % alignof(int) != 0 ||
+      (uintptr_t)d_ecnt % alignof(int) != 0)
+    return bad("misaligned scratch section");
   // what the kernel accumulates into or tests must start at zero
-  if ((e = cudaMemsetAsync(scratch, 0, kHeadBytes + N * kPerSystemBytes, st)) != cudaSuccess)
-    return cuda_bad(e);
+  if ((e = cudaMemsetAsync(scratch, 0, lay.total, st)) != cudaSuccess) return cuda_bad(e);
 
   KArgs a;
   memset(&a, 0, sizeof(a));
@@ -163,10 +175,10 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   a.n_slices = n_slices;
   a.n_skip = n_transient;
   a.h0 = h0;
-  a.queue_head = (unsigned int*)scratch;
+  a.queue_head = (unsigned int*)(scratch + lay.head);
   a.queue_mode = 1;
   a.queue_stride = queue_stride_for(n_systems);
-  a.flags = (int*)(scratch + 64);
+  a.flags = (int*)(scratch + lay.head + 64);
   a.time_limit_ns = (long long)(cfg->time_limit_s * 1e9);
   Props& pr = a.pr;
   for (int i = 0; i < kMaxN; i++) {

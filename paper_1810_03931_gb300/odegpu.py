@@ -26,6 +26,11 @@ ODE_TD_KEEP, ODE_TD_T0_TO_T, ODE_TD_SHIFT = 0, 1, 2
 ODE_OK, ODE_ERR_INVALID_ARG, ODE_ERR_OUT_OF_MEMORY, ODE_ERR_CUDA = 0, -1, -2, -3
 ODE_ERR_NOT_READY, ODE_ERR_TIMEOUT, ODE_ERR_UNSUPPORTED = -4, -5, -6
 
+# (n, P, A, E) of each compiled model: state dimension, parameters,
+# accessories, events (the hooks of Secs. 6.5-6.8; see include/odegpu.h)
+MODEL_DIMS = {ODE_DUFFING: (2, 2, 7, 1), ODE_KELLER_MIKSIS: (2, 13, 4, 1), ODE_VALVE: (3, 5, 5, 2),
+              ODE_BOUNCE: (2, 2, 6, 1), ODE_DUFFING_LYAPUNOV: (4, 2, 5, 1)}
+
 # exported symbols, in the order of the header
 SYMBOLS = (
     "ode_create", "ode_destroy", "ode_query_dims", "ode_num_systems", "ode_set_tolerances",
@@ -351,20 +356,38 @@ def ode_probe_fma_peak(device=0):
 def ode_run_periods_noalloc(settings, n_systems, device, h0, n_transient, n_record, td, y, p, acc,
                             records=None, status=None, accepted=None, stream=None):
     """Integration on caller-owned device arrays with no device allocation
-    (see include/odegpu.h).  Arrays must be CUDA tensors (or device
-    pointers as ints)."""
-    def dev(x, dtype):
+    (see include/odegpu.h).  Arrays must be contiguous CUDA tensors on
+    `device` holding at least the elements the call reads or writes (td 2N,
+    y nN, p PN, acc AN, records n_record (A+n+1) N, status and accepted N),
+    else ODEError(ODE_ERR_INVALID_ARG) is raised before the library is
+    called; raw device pointers (ints) are passed unchecked."""
+    dims = MODEL_DIMS.get(settings.model)
+    N = int(n_systems)
+    if dims is not None and N >= 1:
+        n, P, A, E = dims
+        need = dict(td=2 * N, y=n * N, p=P * N, acc=A * N, records=max(0, n_record) * (A + n + 1) * N,
+                    status=N, accepted=N)
+    else:
+        need = {}  # the library rejects the model or size itself
+
+    def dev(name, x, dtype):
         if x is None or isinstance(x, int):
             return x
-        ptr, kind = _arr(x, dtype)
+        ptr, kind = _arr(x, dtype)  # checks dtype and contiguity
         if kind != ODE_PTR_DEVICE:
             raise ODEError(ODE_ERR_INVALID_ARG, "ode_run_periods_noalloc takes device arrays only")
+        if x.device.index != device:
+            raise ODEError(ODE_ERR_INVALID_ARG, "%s is on cuda:%s, not on device %d" % (name, x.device.index, device))
+        if name in need and x.numel() < need[name]:
+            raise ODEError(ODE_ERR_INVALID_ARG, "%s holds %d elements, the call needs %d"
+                           % (name, x.numel(), need[name]))
         return ptr
     msg = ctypes.c_char_p()
     rc = load().ode_run_periods_noalloc(
-        ctypes.byref(settings), n_systems, device, h0, n_transient, n_record, dev(td, np.float64),
-        dev(y, np.float64), dev(p, np.float64), dev(acc, np.float64), dev(records, np.float64),
-        dev(status, np.int32), dev(accepted, np.int64), _stream(stream), ctypes.byref(msg))
+        ctypes.byref(settings), n_systems, device, h0, n_transient, n_record, dev("td", td, np.float64),
+        dev("y", y, np.float64), dev("p", p, np.float64), dev("acc", acc, np.float64),
+        dev("records", records, np.float64), dev("status", status, np.int32),
+        dev("accepted", accepted, np.int64), _stream(stream), ctypes.byref(msg))
     if rc != ODE_OK:
         raise ODEError(rc, msg.value.decode() if msg.value else "")
     return rc

@@ -11,8 +11,8 @@ import numpy as np
 
 import oracle as O
 from paper_1810_03931_gb300 import odegpu as G
-
-DIMS = {0: (2, 2, 7, 1), 1: (2, 13, 4, 1), 2: (3, 5, 5, 2), 3: (2, 2, 6, 1), 4: (4, 2, 5, 1)}  # n, P, A, E
+from paper_1810_03931_gb300.sweeps import MODEL_DIMS as DIMS  # n, P, A, E
+from paper_1810_03931_gb300.sweeps import km_params as km_params_gpu
 
 
 def _second(w):
@@ -20,17 +20,6 @@ def _second(w):
     pa2 = w.get("PA2", np.zeros(N))
     om2 = w.get("omega2", w["omega"])
     return pa2, om2
-
-
-def km_params_gpu(w):
-    ph = w["phys"]
-    pa2, om2 = _second(w)
-    P = np.zeros((13, w["N"]))
-    for i in range(w["N"]):
-        P[:, i] = G.ode_km_coefficients(w["PA"][i], pa2[i], w["omega"][i], om2[i], 0.0, ph["RE"],
-                                        ph["Pinf"], ph["pV"], ph["sigma"], ph["mu"], ph["rho"], ph["cL"],
-                                        ph["gamma"])
-    return P
 
 
 def km_params_oracle(w):
