@@ -66,6 +66,15 @@ class _Trace(ctypes.Structure):
         ("ev_t", ctypes.POINTER(ctypes.c_double)),
         ("ev_y", ctypes.POINTER(ctypes.c_double)),
         ("ev_y_after", ctypes.POINTER(ctypes.c_double)),
+        ("trial_cap", ctypes.c_int),
+        ("n_trials", ctypes.c_int),
+        ("trial_t", ctypes.POINTER(ctypes.c_double)),
+        ("trial_h", ctypes.POINTER(ctypes.c_double)),
+        ("trial_y", ctypes.POINTER(ctypes.c_double)),
+        ("trial_ynew", ctypes.POINTER(ctypes.c_double)),
+        ("trial_e", ctypes.POINTER(ctypes.c_double)),
+        ("trial_ok", ctypes.POINTER(ctypes.c_int)),
+        ("trial_hnext", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -235,8 +244,11 @@ def run(cfg: Config, td, y, p, acc=None, n_slices=1, n_skip=0, record=False, nth
     return out
 
 
-def trace_slice(cfg: Config, td, y, p, acc=None, cap=1_000_000, ev_cap=100_000):
-    """One slice of ONE system, returning every accepted point and event."""
+def trace_slice(cfg: Config, td, y, p, acc=None, cap=1_000_000, ev_cap=100_000, trial_cap=0):
+    """One slice of ONE system, returning every accepted point and event, and
+    (trial_cap > 0) the first trial_cap trial steps of the adaptive scheme:
+    start time, step size, start state, result, error estimate, outcome
+    (1 accepted, 0 rejected, -1 non-finite) and the step chosen next."""
     n, P, A, E = dims(cfg.model)
     td = np.array(td, dtype=np.float64).reshape(2).copy()
     y = np.array(y, dtype=np.float64).reshape(n).copy()
@@ -251,15 +263,23 @@ def trace_slice(cfg: Config, td, y, p, acc=None, cap=1_000_000, ev_cap=100_000):
     ev_t = np.zeros(ev_cap)
     ev_y = np.zeros((ev_cap, MAXN))
     ev_y_after = np.zeros((ev_cap, MAXN))
+    tc = max(0, int(trial_cap))
+    tt, th, thn = np.zeros(max(tc, 1)), np.zeros(max(tc, 1)), np.zeros(max(tc, 1))
+    ty, tyn, te = (np.zeros((max(tc, 1), MAXN)) for _ in range(3))
+    tok = np.zeros(max(tc, 1), dtype=np.int32)
     tr = _Trace(cap, 0, _dp(tbuf), _dp(ybuf), ev_cap, 0, _ip(ev_index), _dp(ev_t), _dp(ev_y),
-                _dp(ev_y_after))
+                _dp(ev_y_after), tc, 0, _dp(tt), _dp(th), _dp(ty), _dp(tyn), _dp(te), _ip(tok), _dp(thn))
     st = lib().orc_trace_slice(ctypes.byref(cfg), _dp(td), _dp(y), _dp(p), _dp(acc), _ip(ecnt),
                                _lp(nacc), _lp(nrej), ctypes.byref(tr))
     k, m = tr.n_points, tr.n_events
     return dict(status=st, td=td, y=y, acc=acc, ecnt=ecnt[:E].copy(), nacc=int(nacc[0]),
                 nrej=int(nrej[0]), t=tbuf[:k].copy(), ys=ybuf[:k, :n].copy(),
                 ev_index=ev_index[:m].copy(), ev_t=ev_t[:m].copy(), ev_y=ev_y[:m, :n].copy(),
-                ev_y_after=ev_y_after[:m, :n].copy())
+                ev_y_after=ev_y_after[:m, :n].copy(),
+                trials=dict(t=tt[:tr.n_trials].copy(), h=th[:tr.n_trials].copy(),
+                            y=ty[:tr.n_trials, :n].copy(), ynew=tyn[:tr.n_trials, :n].copy(),
+                            e=te[:tr.n_trials, :n].copy(), ok=tok[:tr.n_trials].copy(),
+                            hnext=thn[:tr.n_trials].copy()))
 
 
 def single_step(cfg: Config, t, y, p, h):

@@ -100,7 +100,34 @@ typedef struct orc_trace {
     double *ev_t;      /* [ev_cap] */
     double *ev_y;      /* [ev_cap * ORC_MAXN], state before the action */
     double *ev_y_after; /* [ev_cap * ORC_MAXN], state after it (may be NULL) */
+    /* trial steps of the adaptive scheme (all may be NULL / 0) */
+    int trial_cap;
+    int n_trials;
+    double *trial_t;     /* [trial_cap] start time of the trial */
+    double *trial_h;     /* [trial_cap] its step size */
+    double *trial_y;     /* [trial_cap * ORC_MAXN] state at the start */
+    double *trial_ynew;  /* [trial_cap * ORC_MAXN] fifth-order result */
+    double *trial_e;     /* [trial_cap * ORC_MAXN] embedded error estimate */
+    int *trial_ok;       /* [trial_cap] 1 accepted, 0 rejected, -1 non-finite */
+    double *trial_hnext; /* [trial_cap] step size the controller chose next */
 } orc_trace;
+
+/* Record one trial step of the adaptive scheme in the trace (tests only). */
+static void record_trial(orc_trace *tr, int n, double t, double hs, const double *y,
+                         const double *ynew, const double *e, int ok, double hnext)
+{
+    if (!tr || !tr->trial_t || tr->n_trials >= tr->trial_cap) return;
+    int k = tr->n_trials++;
+    tr->trial_t[k] = t;
+    tr->trial_h[k] = hs;
+    for (int m = 0; m < n; m++) {
+        tr->trial_y[k * ORC_MAXN + m] = y[m];
+        tr->trial_ynew[k * ORC_MAXN + m] = ynew[m];
+        tr->trial_e[k * ORC_MAXN + m] = e[m];
+    }
+    tr->trial_ok[k] = ok;
+    tr->trial_hnext[k] = hnext;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Model dimensions (Sec. 2 and the hooks of Sec. 6.5-6.8).                  */
@@ -454,8 +481,13 @@ static int integrate_slice(const orc_config *c, int n, int A, int E,
             int at_min = hs <= c->hmin;
             if (!isfinite(err) || !all_finite(n, ynew)) {
                 (*nrej)++;
-                if (at_min) { status = ORC_ST_HMIN_NAN; break; }
+                if (at_min) {
+                    record_trial(tr, n, t, hs, y, ynew, e, -1, hs);
+                    status = ORC_ST_HMIN_NAN;
+                    break;
+                }
                 h = fmax(c->shrink * hs, c->hmin);
+                record_trial(tr, n, t, hs, y, ynew, e, -1, h);
                 continue;
             }
             double fac = (err == 0.0) ? c->grow : 0.9 * pow(err, -0.2);
@@ -463,9 +495,11 @@ static int integrate_slice(const orc_config *c, int n, int A, int E,
             if (err > 1.0 && !at_min) {
                 (*nrej)++;
                 h = clampd(hs * fac, c->hmin, c->hmax);
+                record_trial(tr, n, t, hs, y, ynew, e, 0, h);
                 continue;
             }
             hnext = clampd(hs * fac, c->hmin, c->hmax);
+            record_trial(tr, n, t, hs, y, ynew, e, 1, hnext);
         } else if (!all_finite(n, ynew)) {
             /* the fixed RK4 step is also the minimum step */
             (*nrej)++;

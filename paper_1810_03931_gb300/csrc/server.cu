@@ -15,8 +15,10 @@
 // Chunks of different requests and models run concurrently on the device; a
 // request's next chunk is launched as soon as its previous chunk completes,
 // so requests never wait for each other's slow systems.  A finished request is
-// copied out asynchronously on its stream and its slots are reused at once
-// (stream order keeps the copy ahead of any later use of those slots).
+// copied out asynchronously on its stream; its slots return to the free list
+// only once that copy has completed (its event has fired), because the next
+// occupant of the range may be admitted on another stream, whose copies and
+// launches stream order would not keep behind the pending copy.
 //
 // Each system's arithmetic does not depend on its slot, its neighbours or the
 // chunk boundaries (every slice restarts from its own state), so a request's
@@ -308,7 +310,23 @@ int harvest(ode_server* s, Pool& pl, Request* r) {
                          cudaMemcpyDeviceToHost, stream));
   SCK(s, cudaEventRecord(r->done_ev, stream));
   r->harvesting = true;
-  give_range(pl, r->off, r->n);
+  // the slot range is released in release_harvested(), after done_ev
+  return ODE_OK;
+}
+
+// Requests whose results have arrived: mark them done and only now return
+// their slot ranges to the pool's free list.
+int release_harvested(ode_server* s) {
+  for (auto& kv : s->reqs) {
+    Request* r = kv.second;
+    if (!r->harvesting || r->state == kDone) continue;
+    cudaError_t q = cudaEventQuery(r->done_ev);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return scuda(s, q, "harvest");
+    r->state = kDone;
+    r->t_done = now_s();
+    give_range(s->pools[r->model], r->off, r->n);
+  }
   return ODE_OK;
 }
 
@@ -458,6 +476,8 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
   if (!s) return ODE_ERR_INVALID_ARG;
   if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
   int running = 0, waiting = 0;
+  // 0. finished copies out free their slots before anything is admitted
+  if (int rc = release_harvested(s)) return rc;
   for (Pool& pl : s->pools) {
     if (!pl.on) continue;
     // 1. requests whose chunk finished: next chunk, or copy out when done
@@ -493,19 +513,8 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
     running += (int)pl.running.size();
     waiting += (int)pl.waiting.size();
   }
-  // 3. requests whose results have arrived
-  for (auto& kv : s->reqs) {
-    Request* r = kv.second;
-    if (r->harvesting && r->state != kDone) {
-      cudaError_t q = cudaEventQuery(r->done_ev);
-      if (q == cudaSuccess) {
-        r->state = kDone;
-        r->t_done = now_s();
-      } else if (q != cudaErrorNotReady) {
-        return scuda(s, q, "harvest");
-      }
-    }
-  }
+  // 3. requests whose results have arrived in this pass
+  if (int rc = release_harvested(s)) return rc;
   if (n_running) *n_running = running;
   if (n_waiting) *n_waiting = waiting;
   return ODE_OK;

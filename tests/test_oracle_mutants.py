@@ -58,6 +58,14 @@ MUTANTS = [
       P.test_lyapunov_linear_oscillator_exponent_is_minus_half_damping]),
     ("rk4_stage_time", "RK4_C[4] = {0.0, 0.5, 0.5, 1.0};", "RK4_C[4] = {0.0, 0.5, 0.5, 0.5};",
      [P.test_linear_oscillator_rk4_error_bound]),
+    ("controller_safety_0p8", "0.9 * pow(err, -0.2)", "0.8 * pow(err, -0.2)",
+     [P.test_controller_settles_at_its_fixed_point, P.test_controller_next_step_recomputed_from_each_trial]),
+    ("controller_exponent_quarter", "0.9 * pow(err, -0.2)", "0.9 * pow(err, -0.25)",
+     [P.test_controller_settles_at_its_fixed_point, P.test_controller_next_step_recomputed_from_each_trial]),
+    ("secondary_event_not_rechecked", "det[j] = det[j] && crossed(c, j, F[j], Fn[j]);", "det[j] = det[j];",
+     [P.test_second_event_fires_at_the_located_point_only_if_crossed_there]),
+    ("secondary_event_dropped", "det[j] = det[j] && crossed(c, j, F[j], Fn[j]);", "det[j] = 0;",
+     [P.test_second_event_crossed_before_the_located_point_fires_with_it]),
 ]
 
 

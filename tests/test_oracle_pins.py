@@ -425,6 +425,74 @@ def test_controller_step_counts_grow_as_tolerance_tightens():
         assert 1.8 < counts[i + 1] / counts[i] < 3.5
 
 
+# Cash-Karp (1990) coefficients as published, in exact rationals, for the
+# pins below (independent of the oracle's own tableau).
+_CK_A = {(1, 0): Fraction(1, 5), (2, 0): Fraction(3, 40), (2, 1): Fraction(9, 40), (3, 0): Fraction(3, 10),
+         (3, 1): Fraction(-9, 10), (3, 2): Fraction(6, 5), (4, 0): Fraction(-11, 54), (4, 1): Fraction(5, 2),
+         (4, 2): Fraction(-70, 27), (4, 3): Fraction(35, 27), (5, 0): Fraction(1631, 55296),
+         (5, 1): Fraction(175, 512), (5, 2): Fraction(575, 13824), (5, 3): Fraction(44275, 110592),
+         (5, 4): Fraction(253, 4096)}
+_CK_B5 = [Fraction(37, 378), 0, Fraction(250, 621), Fraction(125, 594), 0, Fraction(512, 1771)]
+_CK_B4 = [Fraction(2825, 27648), 0, Fraction(18575, 48384), Fraction(13525, 55296), Fraction(277, 14336),
+          Fraction(1, 4)]
+
+
+def _ck_error_polynomial():
+    """Coefficients P_k (k = 1..6) of the embedded error estimate on y' = lam y:
+    e = P(z) y_n with z = lam h and P_k = (b5 - b4)^T A^(k-1) 1."""
+    e = [Fraction(x) - Fraction(y) for x, y in zip(_CK_B5, _CK_B4)]
+    v = [Fraction(1)] * 6
+    coef = []
+    for _ in range(6):
+        coef.append(sum(e[i] * v[i] for i in range(6)))
+        v = [sum(_CK_A.get((i, j), Fraction(0)) * v[j] for j in range(6)) for i in range(6)]
+    return coef
+
+
+def _controller_next(h, err, shrink=0.1, grow=5.0, hmin=1e-12, hmax=1e6):
+    """The next step from the controller law of Sec. 3 / 6.5 (reading: factor
+    0.9 err^(-1/5), clamped to [shrink, grow], step clamped to [hmin, hmax];
+    err = 0 gives the grow limit)."""
+    fac = grow if err == 0.0 else min(max(0.9 * math.pow(err, -0.2), shrink), grow)
+    return min(max(h * fac, hmin), hmax)
+
+
+def test_controller_next_step_recomputed_from_each_trial():
+    """Every trial step's next step size (accepted and rejected ones) equals
+    the controller law applied to that trial's own error vector, with the
+    error ratio max_m |e_m| / (atol + rtol max(|y_n,m|, |y_n+1,m|))."""
+    cfg = O.make_config(O.DUFFING, O.RKCK45, 1.0, rtol=1e-9, atol=1e-9, mc=(-1.0, 0.0, 1.0))
+    r = O.trace_slice(cfg, [0.0, 30.0], [1.0, 0.0], [0.05, 0.0], trial_cap=100000)
+    T = r["trials"]
+    assert (T["ok"] == 0).sum() >= 1 and (T["ok"] == 1).sum() > 100  # h0 = 1 is rejected first
+    for k in range(len(T["h"])):
+        sc = 1e-9 + 1e-9 * np.maximum(np.abs(T["y"][k]), np.abs(T["ynew"][k]))
+        err = max(abs(T["e"][k][m]) / sc[m] for m in range(2))
+        assert (err > 1.0) == (T["ok"][k] == 0)
+        assert _controller_next(T["h"][k], err) == T["hnext"][k], k
+
+
+def test_controller_settles_at_its_fixed_point():
+    """On y2' = -y2 (Duffing with delta = c3 = B = 0, k = 1) the embedded error
+    is P(-h) y2 with P fixed by the published tableau, so with a pure relative
+    tolerance the error ratio depends on h alone and the controller
+    h <- 0.9 err^(-1/5) h settles where err = 0.9^5.  The steady step of the
+    oracle must equal that root (a safety factor of 0.8 moves it by 11 %, an
+    exponent of -1/4 by 2 %)."""
+    from scipy.optimize import brentq
+    coef = _ck_error_polynomial()
+    assert coef[:4] == [0, 0, 0, 0] and coef[4] != 0  # fourth-order embedded estimate
+    rtol = 1e-10
+    P = lambda z: sum(float(coef[k]) * z ** (k + 1) for k in range(6))
+    hstar = brentq(lambda h: abs(P(-h)) / rtol - 0.9 ** 5, 1e-4, 2.0)
+    cfg = O.make_config(O.DUFFING, O.RKCK45, 1e-2, rtol=rtol, atol=1e-30, mc=(0.0, 0.0, 1.0))
+    r = O.trace_slice(cfg, [0.0, 30.0], [0.0, 1.0], [1.0, 0.0], trial_cap=100000)
+    T = r["trials"]
+    sel = (T["ok"] == 1) & (T["t"] > 5.0) & (T["t"] < 25.0)
+    assert sel.sum() > 300
+    np.testing.assert_allclose(T["h"][sel], hstar, rtol=1e-7)
+
+
 def test_nan_rejects_and_stops_at_hmin():
     cfg = O.make_config(O.DUFFING, O.RKCK45, 1e-2, hmin=1e-6)
     r = O.run(cfg, [[0.0], [1.0]], [[-0.5], [0.1]], [[float("nan")], [0.3]])
@@ -592,6 +660,65 @@ def _valve_cfg(**kw):
 def _valve_params(q):
     v = GOLD["valve"]
     return [[v["kappa"]], [v["delta"]], [v["beta"]], [q], [v["r"]]]
+
+
+def _valve_two_event_trace(direction, y0, delta, T=3.0):
+    """One valve slice with both events on and a fixed step h = 1 long enough
+    to cross both event surfaces in one step (kappa 1.25, beta 0.1, q 1,
+    r 0.8; event tolerances 1e-10).  Also returns the end of that first step
+    without location, to show both surfaces were crossed in it."""
+    p = [1.25, delta, 0.1, 1.0, 0.8]
+    cfg = O.make_config(O.VALVE, O.RKCK45, 1.0, rtol=1e-6, atol=1e-6, hmin=1.0, hmax=1.0, events_on=True,
+                        evt_dir=direction, evt_tol=(1e-10, 1e-10), evt_stop=(0, 0), max_eq=0)
+    y1, _ = O.single_step(cfg, 0.0, y0, p, 1.0)
+    return O.trace_slice(cfg, [0.0, T], y0, p), p, y1
+
+
+def _valve_free_flight(p, y0, T):
+    """Independent integration of Eqs. (29)-(31) without events (scipy)."""
+    from scipy.integrate import solve_ivp
+    kap, dl, bt, q, _ = p
+    f = lambda t, y: [y[1], -kap * y[1] - (y[0] + dl) + y[2], bt * (q - y[0] * math.sqrt(max(y[2], 0.0)))]
+    grid = np.linspace(0.0, T, 300001)
+    return grid, solve_ivp(f, (0.0, T), y0, method="DOP853", rtol=1e-12, atol=1e-13, t_eval=grid).y
+
+
+def test_second_event_fires_at_the_located_point_only_if_crossed_there():
+    """Sec. 4: when several events are detected in one step only the highest
+    index is located.  Here one step of size 1 first crosses the impact
+    surface y1 = 0 (event 1, downwards) and only later (on the un-impacted
+    flow) the minimum y2 = 0 (event 0, upwards).  At the located impact y2 is
+    still negative, so event 0 must not fire there; brute force on an
+    independent integration confirms that y2 < 0 all the way to the impact."""
+    y0 = [0.01, -1.0, 1.0]
+    r, p, yend = _valve_two_event_trace((+1, -1), y0, delta=0.5)
+    assert yend[0] < 0.0 and yend[1] > 0.0  # the whole step crossed both surfaces
+    grid, Y = _valve_free_flight(p, y0, 1.0)
+    i = int(np.argmax(Y[0] <= 0.0))  # first grid point past the impact
+    assert i > 0 and np.all(Y[1][: i + 1] < 0.0)
+    # the one-step location is within the step's own accuracy of the impact
+    assert r["ev_index"][0] == 1 and abs(r["ev_t"][0] - grid[i]) < 1e-3
+    # ... and the minimum of the flow without the impact comes later in that step
+    assert np.any(Y[1][i:] > 0.0)
+    assert 0 not in list(r["ev_index"][r["ev_t"] <= r["ev_t"][0]])
+
+
+def test_second_event_crossed_before_the_located_point_fires_with_it():
+    """The other case of the same rule: the step first passes a maximum
+    (event 0, y2 falling through 0) and then the impact (event 1).  Event 1 is
+    located; event 0 is still crossed at that point and fires there, in
+    ascending order, before the impact action."""
+    y0 = [0.05, 0.1, 1.0]
+    r, p, yend = _valve_two_event_trace((-1, -1), y0, delta=2.0)
+    assert yend[0] < 0.0 and yend[1] < 0.0  # the whole step crossed both surfaces
+    grid, Y = _valve_free_flight(p, y0, 1.0)
+    i_max = int(np.argmax(Y[1] <= 0.0))
+    i_imp = int(np.argmax(Y[0] <= 0.0))
+    assert 0 < i_max < i_imp  # maximum first, impact later, both within the first step
+    assert list(r["ev_index"][:2]) == [0, 1]
+    assert r["ev_t"][0] == r["ev_t"][1] and abs(r["ev_t"][1] - grid[i_imp]) < 1e-3
+    # event 0 saw the pre-action state (y2 < 0), the impact then reversed y2
+    assert r["ev_y"][0][1] < 0 and r["ev_y_after"][1][1] == -0.8 * r["ev_y"][1][1]
 
 
 def test_valve_high_flow_rate_settles_to_equilibrium():

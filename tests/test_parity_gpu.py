@@ -685,3 +685,25 @@ def test_kernels_do_not_spill():
                     info = G.ode_kernel_info(model, scheme, prec, pers)
                     assert info["blocks_per_sm"] >= 1
                     assert info["regs"] <= 255
+
+
+@pytest.mark.parametrize("case", ["second_not_crossed_at_located_point", "second_crossed_before_it"])
+def test_valve_two_events_in_one_step_parity(case):
+    """Both event surfaces crossed within one fixed step of size 1 (Sec. 4):
+    only the impact (highest index) is located; the other event fires at the
+    located point only if it is crossed there.  Event counts, accessories and
+    the end state equal the oracle's (the oracle pins this rule by brute
+    force)."""
+    direction, y0, delta = {"second_not_crossed_at_located_point": ((1, -1), [0.01, -1.0, 1.0], 0.5),
+                            "second_crossed_before_it": ((-1, -1), [0.05, 0.1, 1.0], 2.0)}[case]
+    N = 4  # the same system four times: one partial warp
+    p = np.tile(np.array([[1.25], [delta], [0.1], [1.0], [0.8]]), (1, N))
+    w = dict(W.valve(N=N, n_transient=0, n_record=1), p=p, rtol=1e-6, atol=1e-6, hmin=1.0, hmax=1.0,
+             h0=1.0, evt_dir=direction, evt_tol=(1e-10, 1e-10), evt_stop=(0, 0), max_eq=0, td_mode=W.TD_KEEP,
+             td=np.vstack([np.zeros(N), np.full(N, 3.0)]), y0=np.tile(np.array(y0)[:, None], (1, N)))
+    g = run_gpu(w)
+    o = run_oracle(w, 1)
+    np.testing.assert_array_equal(g["ecnt"], o["ecnt"])
+    np.testing.assert_array_equal(g["status"], o["status"])
+    np.testing.assert_array_equal(g["acc"][4], o["acc"][4])  # impacts
+    np.testing.assert_allclose(g["y"], o["y"], rtol=1e-8, atol=1e-8)

@@ -8,32 +8,11 @@ import pytest
 
 import workloads as W
 from paper_1810_03931_gb300 import odegpu as G
+from paper_1810_03931_gb300.sweeps import settings_for
 
 from _runners import DIMS, km_params_gpu, run_gpu
 
 pytestmark = pytest.mark.gpu
-
-
-def settings_for(w):
-    n, P, A, E = DIMS[w["model"]]
-    s = G.NoAllocSettings()
-    s.model, s.scheme, s.prec = w["model"], w["scheme"], G.ODE_FP64
-    for i in range(4):
-        s.rtol[i] = w["rtol"]
-        s.atol[i] = w["atol"]
-    s.h_max, s.h_min, s.grow_limit, s.shrink_limit = w["hmax"], w["hmin"], w["grow"], w["shrink"]
-    s.events_enabled = int(w["events_on"])
-    for j in range(min(E, 2)):
-        s.direction[j] = w["evt_dir"][j]
-        s.tolerance[j] = w["evt_tol"][j]
-        s.stop_count[j] = w["evt_stop"][j]
-    s.max_steps_in_zone = w["max_eq"]
-    s.time_domain_mode = w["td_mode"]
-    s.max_steps_per_slice = 10**9
-    s.time_limit_s = 300.0
-    for i, c in enumerate(w["mc"]):
-        s.model_constants[i] = c
-    return s
 
 
 def make_server(slice_periods=3):
@@ -144,3 +123,47 @@ def test_tuned_chunk_length_and_a_lyapunov_pool():
     ref = run_gpu(wl, persistent=0)
     np.testing.assert_array_equal(out[0][1]["y"], ref["y"])
     np.testing.assert_array_equal(out[0][1]["acc"], ref["acc"])
+
+
+def test_reused_slot_range_with_distinct_requests_matches_oracle():
+    """A pool of 256 slots and three 200-system requests with distinct seeds:
+    each request reuses the range the previous one held (it may be admitted on
+    another stream while the previous results are still being copied out).
+    Each request's end state and accessories are checked bitwise against a
+    plain ode_run_periods of the same systems and against the CPU oracle
+    (100 x rtol on well-conditioned points, counts exact)."""
+    from _runners import run_oracle
+    from test_parity_gpu import NTHREADS, _nonchaotic
+
+    horizon = 4
+    srv = G.ode_server_create(0, 1 << 30, 1)
+    reqs = {}
+    try:
+        G.ode_server_add_model(srv, settings_for(W.duffing_rkck(1, 1, 0, 1)), 1e-2, 256)
+        for sd in (31, 32, 33):
+            w, p = request(W.DUFFING, 200, horizon, sd)
+            reqs[G.ode_server_submit(srv, W.DUFFING, horizon, w["td"], w["y0"], p)] = w
+        G.ode_server_progress(srv)
+        states = [G.ode_server_poll(srv, t) for t in reqs]
+        assert states.count(1) == 1 and states.count(0) == 2  # one range, one request at a time
+        res = drain(srv, {t: (W.DUFFING, 200) for t in reqs})
+    finally:
+        G.ode_server_destroy(srv)
+    for t, w in reqs.items():
+        got = res[t]
+        ww = dict(w, n_transient=horizon - 1, n_record=1)
+        ref = run_gpu(ww, persistent=0)
+        for key in ("td", "y", "acc", "status", "nacc"):
+            np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
+        mask, o = _nonchaotic(ww, horizon - 1, 1, cont_rows=(4, 5, 7, 8), rtol=1e-10)
+        assert mask.sum() >= 150
+        tol = 100 * 1e-10
+        for m in range(2):
+            assert np.all(np.abs(got["y"][m, mask] - o["y"][m, mask]) <= tol * (1 + np.abs(o["y"][m, mask])))
+        for a in (4, 5):  # first located maximum of the last period and its time
+            assert np.all(np.abs(got["acc"][a, mask] - o["acc"][a, mask])
+                          <= tol * (1 + np.abs(o["acc"][a, mask])))
+        np.testing.assert_array_equal(got["acc"][6, mask], o["acc"][6, mask])  # maxima counted
+        np.testing.assert_array_equal(got["status"], o["status"])
+        # the requests differ, so a late copy of a previous occupant would show
+        assert not np.array_equal(got["y"], res[list(reqs)[0]]["y"]) or t == list(reqs)[0]
