@@ -186,6 +186,16 @@ int ode_set_time_limit(ode_solver *s, double seconds);
  * Results do not depend on the shape. */
 int ode_set_launch(ode_solver *s, int block_size, int persistent);
 
+/* Work split of a launch (no counterpart in the paper, whose launch gives
+ * every thread one system and runs one Solve per launch, Sec. 6.4):
+ * systems_per_thread in [1, 64] for the per-sweep launch (thread g of G takes
+ * systems g, g + G, g + 2G, ... one after another; the persistent launches
+ * ignore it), and slices_per_launch >= 0 for ode_run_periods (the run is split
+ * into launches of that many slices, each launch storing and reloading the
+ * whole state; 0 = all slices in one launch).  Results do not depend on
+ * either.  Defaults 1 and 0. */
+int ode_set_schedule(ode_solver *s, int systems_per_thread, int slices_per_launch);
+
 /* ---- filling and reading the object (Sec. 6.3, 6.10) --------------------- */
 
 /* LinearSet: copy `count` consecutive systems from a pool of `pool_size`
@@ -238,15 +248,21 @@ int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, dou
 
 /* Autotuner: integrate n_slices slices from the current state with every
  * launch shape of a fixed candidate list -- block size 64, 96, 128, 160,
- * 192, 256, each per-sweep and persistent with queue order 1 and 2 (shapes
- * the kernel cannot launch are skipped) -- timed with CUDA events on
- * `stream`, then restore the state, status and counters and keep the fastest
- * shape (as ode_set_launch would).  Outputs (may be NULL): the chosen block
- * size and persistent value, and trial_ms[18] = milliseconds per trial in the
- * order [persistent 0, 1, 2][block] (-1 for skipped shapes).  Allocates a
- * temporary copy of the state.  Synchronous. */
+ * 192, 256 for each of four forms: per-sweep with 1 and with 2 systems per
+ * thread, persistent with queue order 1 and 2 (shapes the kernel cannot
+ * launch are skipped) -- then, for the fastest shape, the same slices split
+ * into launches of 1 and of ceil(n_slices / 2) slices; every trial is timed
+ * with CUDA events on `stream` and starts from the same saved state, which is
+ * restored at the end (state, status and counters).  The fastest shape and
+ * split are kept (as ode_set_launch and ode_set_schedule would set them).
+ * Outputs (may be NULL): block size, persistent value, systems per thread,
+ * slices per launch (0 = all), and trial_ms[27] = milliseconds per trial:
+ * [form][block] for the 4 x 6 shapes in the order above, then the splits
+ * [1 slice, ceil(n_slices / 2) slices, all] (-1 for skipped trials).
+ * Allocates a temporary copy of the state.  Synchronous. */
 int ode_autotune(ode_solver *s, double h0, int n_slices, void *stream, int *block_size,
-                 int *persistent, double *trial_ms);
+                 int *persistent, int *systems_per_thread, int *slices_per_launch,
+                 double *trial_ms);
 
 /* Wait for all work this solver enqueued. */
 int ode_synchronize(ode_solver *s);
@@ -332,20 +348,27 @@ typedef struct ode_noalloc_settings {
  * in HBM (the pools together must fit in the server's HBM budget: admission
  * by footprint).  A request of n systems and n_periods periods waits (FIFO per
  * model) until a contiguous range of n free slots exists, is then copied into
- * it and stays resident there.  It advances in chunks of slices, each one
- * launch over its slot range (a CUDA graph captured at admission and
- * replayed) on one of the server's streams; chunks of different requests and
- * models run concurrently and a request's next chunk starts as soon as its
- * previous one completes.  When its horizon is done a request is copied out
- * asynchronously and its slots are reused at once.  A request's results are
- * those of ode_run_periods with n_transient = n_periods - 1, n_record = 1
- * (same per-system arithmetic), alone or in any mix.
+ * it and stays resident there.  Its systems are merged into ONE persistent
+ * launch per model (a resident serving kernel whose threads take systems from
+ * a ring of slot indices that the host keeps filling while the kernel runs):
+ * a thread that finishes a system takes the next one at once, whatever
+ * request it belongs to, so requests that arrive while others run share the
+ * same launch.  Systems of different requests are published to the ring in
+ * round-robin chunks, so a small request is not queued behind a large one.
+ * The GPU is split between models with work (max-min fair shares of the SMs);
+ * a model that gets work while others hold the GPU has them stop at their
+ * next slice boundary and relaunch with the new split.  When all n systems of
+ * a request are done its results are copied out asynchronously; its slots
+ * are reused once that copy has completed.  A request's results are those of
+ * ode_run_periods with n_transient = n_periods - 1, n_record = 1 (same
+ * per-system arithmetic, restarted per slice), alone or in any mix.
  * The caller drives the loop with ode_server_progress (non-blocking). */
 typedef struct ode_server ode_server;
 
-/* device, HBM budget for the pools (bytes), slices per chunk: >= 1 fixed, or
- * 0 = tuned per request (every chunk is timed and the next one sized to take
- * about 25 ms; the first chunk is one slice). */
+/* device, HBM budget for the pools (bytes), and the residency quantum
+ * slice_periods: 0 = a thread keeps a system for its whole horizon; k >= 1 =
+ * a system goes back to the ring after k slices (time slicing between the
+ * systems waiting for threads; results are the same either way). */
 int ode_server_create(ode_server **out, int device, long long hbm_budget_bytes, int slice_periods);
 
 /* Serve a model with the settings of ode_run_periods_noalloc (the settings'
@@ -359,9 +382,11 @@ int ode_server_add_model(ode_server *s, const ode_noalloc_settings *settings, do
 int ode_server_submit(ode_server *s, int model, int n_systems, int n_periods, const double *td,
                       const double *y0, const double *p, long long *ticket);
 
-/* One non-blocking pass of the loop: launch the next chunk of every request
- * whose chunk completed, copy out finished requests, admit waiting ones.  Outputs the
- * numbers of resident and waiting requests (may be NULL). */
+/* One non-blocking pass of the loop: read the last snapshot of the done
+ * counters and yielded systems (finished requests are copied out), admit
+ * waiting requests, publish systems to the rings, start, grow or rebalance the
+ * serving kernels, and start the next snapshot.  Outputs the numbers of
+ * resident and waiting requests (may be NULL). */
 int ode_server_progress(ode_server *s, int *n_running, int *n_waiting);
 
 /* State of a request: 0 waiting, 1 running, 2 done. */
@@ -374,6 +399,14 @@ int ode_server_poll(ode_server *s, long long ticket, int *state);
 int ode_server_result(ode_server *s, long long ticket, double *td, double *y, double *acc,
                       int *status, long long *accepted, double *latency_s);
 
+/* Counters of one served model (out[8]): serving-kernel instances started,
+ * stop requests (rebalancing), systems taken back from the yield list,
+ * snapshots read, ring entries published, requests copied out, flags seen
+ * (1 watchdog stop, 2 an entry outside the pool), systems not yet counted. */
+int ode_server_stats(const ode_server *s, int model, long long *out);
+
+/* Stop the serving kernels at their next slice boundary, wait for them and
+ * free everything (unfinished requests are dropped). */
 int ode_server_destroy(ode_server *s);
 const char *ode_server_last_error(const ode_server *s);
 

@@ -338,3 +338,26 @@ def km_coefficients(PA1, omega1, PA2=0.0, omega2=None, theta=0.0, **phys):
                                   ph["cL"], ph["gamma"], _dp(C))
         out[:, i] = C
     return out
+
+
+def run_workload(w, nthreads=8, record=True, n_transient=None, n_record=None, **cfg_over):
+    """Run a seeded sweep description (the ``workloads`` dictionaries) through
+    the oracle: its settings, time domains, initial conditions and parameters
+    (Keller-Miksis coefficients from this module's own Eqs. 16-28 code).
+    ``cfg_over`` overrides settings (e.g. rtol, atol)."""
+    n_tr = w["n_transient"] if n_transient is None else n_transient
+    n_rec = w["n_record"] if n_record is None else n_record
+    ww = dict(w)
+    ww.update(cfg_over)
+    cfg = make_config(ww["model"], ww["scheme"], ww["h0"], rtol=ww["rtol"], atol=ww["atol"], hmax=ww["hmax"],
+                      hmin=ww["hmin"], grow=ww["grow"], shrink=ww["shrink"], events_on=ww["events_on"],
+                      evt_dir=ww["evt_dir"], evt_tol=ww["evt_tol"], evt_stop=ww["evt_stop"], max_eq=ww["max_eq"],
+                      mc=ww["mc"] or None, td_mode=ww["td_mode"])
+    if w["model"] == KELLER_MIKSIS:
+        N = w["N"]
+        p = km_coefficients(w["PA"], w["omega"], PA2=w.get("PA2", np.zeros(N)),
+                            omega2=w.get("omega2", w["omega"]), theta=0.0, **w["phys"])
+    else:
+        p = w["p"]
+    return run(cfg, w["td"], w["y0"], p, None, n_slices=n_tr + n_rec, n_skip=n_tr, record=record,
+               nthreads=nthreads)

@@ -69,9 +69,38 @@ struct KArgs {
                              // strided 32-system chunks, 2 = one pop per lane
   unsigned int queue_stride; // mode 1: queue chunk c of 32 slots holds systems
                              // 32 * ((c * queue_stride) mod chunks) + 0..31
+  int tab_cap;               // RK4 per-sweep launches: entries of the block-shared
+                             // forcing table in dynamic shared memory (0 = none)
+  int spt;                   // per-sweep launches: systems per thread (<= 1: one);
+                             // thread g takes systems g, g + G, g + 2G, ... (G threads)
   int* flags;                // flags[0] != 0: the watchdog stopped a system
   long long time_limit_ns;   // per-thread run-time limit of one launch (0 = none)
   Props pr;
+};
+
+// Control block of a resident serving kernel (serve.cuh), one per served
+// model, in device memory; word offsets (each on its own 64-byte line).
+enum ServeCtlWord {
+  kCtlRingHead = 0,    // admission-ring entries taken (device compare-and-swap)
+  kCtlRingTail = 16,   // admission-ring entries published (written by the host)
+  kCtlStop = 32,       // != 0: yield at the next slice boundary and exit (host)
+  kCtlYieldTail = 48,  // yield-list entries reserved (device atomics)
+  kCtlFlags = 64,      // watchdog flag
+  kCtlWords = 80
+};
+
+// Arguments of the resident serving kernel besides its KArgs (whose slot
+// arrays are the model's pool; n_slices is the residency quantum).
+struct ServeArgs {
+  const unsigned int* ring;      // [ring_cap] slot indices to run, in order
+  unsigned int ring_cap;
+  unsigned int* ctl;             // control block (ServeCtlWord)
+  unsigned long long* yl;        // [yl_cap] yielded slots: (lap << 32) | slot
+  unsigned int yl_cap;
+  unsigned int* done_cnt;        // per request-table entry: systems finished
+  unsigned int done_cap;         // entries of done_cnt
+  const int* owner;              // [pool capacity] request-table entry of a slot
+  long long idle_ns;             // a warp with no work for this long exits
 };
 
 // Per-model kernel table entry: the kernel function for a (scheme,

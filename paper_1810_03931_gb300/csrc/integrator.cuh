@@ -203,12 +203,14 @@ struct Stepper {
     return st;
   }
 
-  // yb: the state y in precision T (y itself in binary64)
+  // yb: the state y in precision T (y itself in binary64).  tab (RK4 only, or
+  // null): (cos, sin) of omega t at the half-step grid of the slice, the
+  // stages at t + hs / 2 and t + hs being entries tab[1] and tab[2].
   static __device__ __forceinline__ void step(double t, const double (&y)[n], const T (&yb)[n],
                                               double hs, const T (&pt)[P], const T (&mct)[3],
                                               const T (&k1)[n], T C, T S, double w,
                                               double (&ynew)[n], double (&err)[n], double& Cn,
-                                              double& Sn) {
+                                              double& Sn, const double2* tab = nullptr) {
     const T h = (T)hs;
     const T tb = (T)t;
     const double x = w * hs, U = x * x;
@@ -256,7 +258,15 @@ struct Stepper {
     } else {
       T k2[n], k3[n], k4[n];
       const T half = (T)0.5;
-      const Stage<T> sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
+      Stage<T> sh, s4;
+      if (kRotate && tab != nullptr) {
+        const double2 f1 = tab[1], f2 = tab[2];
+        sh.t = t + 0.5 * hs; sh.c = f1.x; sh.s = f1.y;
+        s4.t = t + hs; s4.c = f2.x; s4.s = f2.y;
+      } else {
+        sh = stage_at<1, 2>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
+        s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
+      }
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, half * k1[m]);
       M::template rhs<T>(sh, ys, pt, mct, k2);
@@ -265,7 +275,6 @@ struct Stepper {
       M::template rhs<T>(sh, ys, pt, mct, k3);
 #pragma unroll
       for (int m = 0; m < n; m++) ys[m] = stage(y[m], yb[m], hs, h, k3[m]);
-      const Stage<T> s4 = stage_at<1, 1>(t, hs, tb, h, mct, C, S, w, x, U, small, lo, xw);
       M::template rhs<T>(s4, ys, pt, mct, k4);
       Cn = (double)s4.c;
       Sn = (double)s4.s;
@@ -344,6 +353,7 @@ struct Lane {
   int sys;
   int slice;
   int my_slices;
+  int left0;  // served slots: the slice budget loaded with the slot
   int status;
   bool k1ok;
   bool locating;
@@ -371,28 +381,47 @@ struct Lane {
   T gC, gS;         // binary32 form: cos, sin of omega t at the lane's t
   T yt[n];          // binary32 form: the state y rounded once per accepted point
   double w;         // forcing angular frequency
+  const double2* tab;  // RK4: block-shared (cos, sin) of omega t on the half-step
+                       // grid of the slice time domain (tab_t0, tab_t1), or null
+  int tab_n;           // steps the table covers
+  double tab_t0, tab_t1;
+  bool use_tab;        // this slice lies on the table's grid
 
   // Load the slot; false when the system has no slice to run in this launch.
+  // CG: load through L2 only (ld.global.cg), for slots that other agents (the
+  // host's copies, other SMs) may have rewritten while this kernel runs.
+  template <bool CG = false>
   __device__ __forceinline__ bool load(const KArgs& a) {
     const size_t N = (size_t)a.ld;  // 64-bit component offsets
+    auto ld = [](const double* q) { return CG ? __ldcg(q) : *q; };
     my_slices = a.n_slices;
-    if (a.slices_left != nullptr) my_slices = min(my_slices, a.slices_left[sys]);
+    int my_slices_left = 0;
+    if (a.slices_left != nullptr) {
+      my_slices_left = CG ? __ldcg(a.slices_left + sys) : a.slices_left[sys];
+      my_slices = min(my_slices, my_slices_left);
+    }
+    (void)my_slices_left;
     if (my_slices <= 0) return false;
-    t0 = a.td[sys];
-    t1 = a.td[N + sys];
+    t0 = ld(a.td + sys);
+    t1 = ld(a.td + N + sys);
 #pragma unroll
-    for (int m = 0; m < n; m++) y[m] = a.y[m * N + sys];
+    for (int m = 0; m < n; m++) y[m] = ld(a.y + m * N + sys);
 #pragma unroll
     for (int m = 0; m < P; m++) {
-      p[m] = a.p[m * N + sys];
+      p[m] = ld(a.p + m * N + sys);
       pt[m] = (T)p[m];
     }
     slice = 0;
     nacc = 0;
     nrej = 0;
+    if (CG) left0 = my_slices_left;
     return true;
   }
 
+  // Store the slot.  CG: counters and the slice budget are read through L2
+  // and the budget is written from the value loaded with the slot (another
+  // agent may have rewritten the slot since this SM last cached it).
+  template <bool CG = false>
   __device__ __forceinline__ void store(const KArgs& a) {
     const size_t N = (size_t)a.ld;  // 64-bit component offsets
     a.td[sys] = t0;
@@ -404,9 +433,15 @@ struct Lane {
     a.status[sys] = status;
 #pragma unroll
     for (int j = 0; j < E; j++) a.ecnt[j * N + sys] = a.pr.events_on ? ecnt[j] : 0;
-    a.nacc[sys] += nacc;
-    a.nrej[sys] += nrej;
-    if (a.slices_left != nullptr) a.slices_left[sys] -= slice;
+    if (CG) {
+      a.nacc[sys] = __ldcg(a.nacc + sys) + nacc;
+      a.nrej[sys] = __ldcg(a.nrej + sys) + nrej;
+      if (a.slices_left != nullptr) a.slices_left[sys] = left0 - slice;
+    } else {
+      a.nacc[sys] += nacc;
+      a.nrej[sys] += nrej;
+      if (a.slices_left != nullptr) a.slices_left[sys] -= slice;
+    }
   }
 
   __device__ __forceinline__ void anchor_forcing() {
@@ -443,6 +478,7 @@ struct Lane {
     steps = 0;
     k1ok = false;
     locating = false;
+    if constexpr (SCHEME == kRK4 && St::kRotate) use_tab = tab != nullptr && t0 == tab_t0 && t1 == tab_t1;
     anchor_forcing();
   }
 
@@ -480,6 +516,8 @@ struct Lane {
     t = tnew;
     if constexpr (St::kRotate) {
       if (located) {
+        // a located point is off the fixed-step grid: the table no longer applies
+        if constexpr (SCHEME == kRK4) use_tab = false;
         anchor_forcing();
       } else {
         fC = fCn;
@@ -612,6 +650,13 @@ struct Lane {
         st0.t = t;
         st0.c = fC;
         st0.s = fS;
+        if constexpr (SCHEME == kRK4) {
+          if (use_tab && !locating && steps < tab_n) {
+            const double2 f0 = tab[2 * steps];
+            st0.c = f0.x;
+            st0.s = f0.y;
+          }
+        }
       } else {
         // binary32 forcing anchor at the new t, kept for the trials from t
         if constexpr (M::kForcing != kNoForcing) sincos_quarter(w * t, gS, gC);
@@ -625,7 +670,11 @@ struct Lane {
       k1ok = true;
     }
     double ynew[n], err[n], Cn = 0.0, Sn = 0.0;
-    if constexpr (St::kRotate) St::step(t, y, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn);
+    if constexpr (St::kRotate) {
+      const double2* tb = nullptr;
+      if constexpr (SCHEME == kRK4) tb = (use_tab && !locating && steps < tab_n) ? tab + 2 * steps : nullptr;
+      St::step(t, y, y, hs, pt, mct, k1, fC, fS, w, ynew, err, Cn, Sn, tb);
+    }
     else if constexpr (PREC == kFP64) St::step(t, y, y, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
     else St::step(t, y, yt, hs, pt, mct, k1, gC, gS, w, ynew, err, Cn, Sn);
     if (!locating) {
@@ -792,6 +841,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// Per-sweep launch with spt systems per thread: the system after `sys` for
+// this thread (sys + G with G threads in the grid, at most spt per thread),
+// or N when there is none.  Out of line: it runs once per system and keeps
+// its registers out of the step loop.
+static __device__ __noinline__ int next_static_system(int sys, int N, int spt) {
+  const long long G = (long long)gridDim.x * blockDim.x;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nx = (long long)sys + G;
+  return (nx < N && nx < g + (long long)spt * G) ? (int)nx : N;
+}
+
 // Launch bounds of the integrator kernels: at most ODEGPU_MAX_THREADS per
 // block and at least M::kMinBlocks resident blocks of that size per SM (which
 // caps the registers per thread; more resident warps keep the FP64 pipe fed).
@@ -816,6 +876,72 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
   {
     double mcd[3] = {a.pr.mc[0], a.pr.mc[1], a.pr.mc[2]};
     L.w = M::omega(mcd);
+  }
+  L.tab = nullptr;
+  L.tab_n = 0;
+  L.tab_t0 = L.tab_t1 = 0.0;
+  L.use_tab = false;
+  if constexpr (SCHEME == kRK4 && Stepper<M, SCHEME, PREC>::kRotate) {
+    // Fixed-step RK4 on a shared time grid (the paper's iterated Solve over
+    // forcing periods, Sec. 7.1.1): the forcing at every stage time of the
+    // slice is the same for all systems whose slice has the same (t0, t1), so
+    // the block tabulates (cos, sin)(omega t) at the stage times of one slice
+    // once: that of its first system (per-sweep form) or of system 0
+    // (persistent form, whose systems are not known in advance).  Thread 0 walks the step sequence exactly as a lane
+    // does (t accumulates t + h; the last step is clipped to t1), writing the
+    // times t_i (entry 2 i), t_i + h / 2 (2 i + 1) and the end t_i + h of the
+    // last step (2 n); then the block evaluates them.  Systems on that grid
+    // read the table for their first tab_n steps; others (a different time
+    // domain, another slice in a moving time domain) rotate their own anchor.
+    extern __shared__ double2 s_tab[];
+    if (a.tab_cap > 0) {
+      __shared__ double s_t0, s_t1;
+      __shared__ int s_n;
+      if (threadIdx.x == 0) {
+        const long long first = PERSIST ? 0 : (long long)blockIdx.x * blockDim.x;
+        const int s0 = (int)(first < a.N ? first : a.N - 1);
+        const double t0 = a.td[s0], t1 = a.td[(size_t)a.ld + s0];
+        double nst = ceil((t1 - t0) / a.h0 - 1e-9);
+        nst = nst < 1.0 ? 1.0 : nst;
+        const double h = (t1 - t0) / nst;
+        int ns = 0;
+        bool reached = false;  // the walk ended with the clipped last step
+        if (t0 < t1 && 2.0 * nst + 1.0 <= (double)a.tab_cap) {
+          double t = t0;
+          for (; 2 * ns + 2 < a.tab_cap; ns++) {  // writes entries 2 ns .. 2 ns + 2 < tab_cap
+            s_tab[2 * ns].x = t;
+            if (t1 - t <= h * (1.0 + 1e-9)) {
+              const double hs = t1 - t;
+              s_tab[2 * ns + 1].x = t + 0.5 * hs;
+              s_tab[2 * ns + 2].x = t + hs;
+              ns++;
+              reached = true;
+              break;
+            }
+            s_tab[2 * ns + 1].x = t + 0.5 * h;
+            t = t + h;
+          }
+        }
+        if (!reached) ns = 0;
+        s_t0 = t0;
+        s_t1 = t1;
+        s_n = ns;
+      }
+      __syncthreads();
+      const int ns = s_n;
+      for (int j = threadIdx.x; j <= 2 * ns && ns > 0; j += blockDim.x) {
+        double sj, cj;
+        sincos(L.w * s_tab[j].x, &sj, &cj);
+        s_tab[j] = make_double2(cj, sj);
+      }
+      __syncthreads();
+      if (ns > 0) {
+        L.tab = s_tab;
+        L.tab_n = ns;
+        L.tab_t0 = s_t0;
+        L.tab_t1 = s_t1;
+      }
+    }
   }
 
   // Persistent form, two queue orders (the autotuner tries both):
@@ -846,6 +972,9 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
     }
   };
   bool active;
+  // per-sweep form with several systems per thread: the k-th system of thread
+  // g is g + k G (G threads in the grid), so a warp always holds neighbours;
+  // k follows from the system index, so no register carries it
   if constexpr (PERSIST) {
     L.sys = pop();
   } else {
@@ -863,6 +992,11 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
       fresh = active;
     } else {
       active = false;
+      if (a.spt > 1) {
+        L.sys = next_static_system(L.sys, a.N, a.spt);
+        active = L.sys < a.N;
+        fresh = active;
+      }
     }
   };
   auto settle = [&]() {
@@ -907,9 +1041,17 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
   }
 }
 
-// Kernel lookup for one model: every (scheme, precision, persistent) variant.
+}  // namespace odegpu
+
+#include "serve.cuh"
+
+namespace odegpu {
+
+// Kernel lookup for one model: every (scheme, precision, launch form) variant;
+// launch form 3 is the resident serving kernel.
 template <class M>
 const void* lookup_kernel(int scheme, int prec, int persistent) {
+  if (persistent == 3) return lookup_serve_kernel<M>(scheme, prec);
   if (prec == kFP64) {
     if (scheme == kRK4)
       return persistent ? (const void*)ode_kernel<M, kRK4, kFP64, true>

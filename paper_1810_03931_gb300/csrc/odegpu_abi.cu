@@ -62,6 +62,8 @@ struct ode_solver {
   size_t stage_cap = 0;         // bytes
   int block_size = 0;           // 0 = automatic
   int persistent = 0;
+  int spt = 1;                  // per-sweep launches: systems per thread
+  int slices_per_launch = 0;    // ode_run_periods: slices per launch (0 = all in one)
   double time_limit_s = 600.0;  // watchdog limit per thread and launch
   std::string err;
 };
@@ -316,12 +318,27 @@ int random_copy(ode_solver* s, const int* idx_obj, const int* idx_pool, int pool
   return ODE_OK;
 }
 
-// Blocks per SM and block size for a launch of `fn`.
-int launch_shape(ode_solver* s, const void* fn, int* block, int* blocks_per_sm, int* sms) {
+// Entries of the block-shared RK4 forcing table (Sec. 7.1.1's fixed-step
+// loop over forcing periods): 2 n + 1 (cos, sin) pairs cover n steps per
+// slice; 2049 pairs (32 KB of shared memory) cover up to 1024 steps.
+constexpr int kForcingTable = 2049;
+
+// Table entries for a launch of this solver: binary64 RK4 of a forced model
+// whose slices keep their time domain (every slice on the same grid), else 0.
+int forcing_table_entries(const ode_solver* s) {
+  const bool forced = s->model == ODE_DUFFING || s->model == ODE_DUFFING_LYAPUNOV ||
+                      s->model == ODE_KELLER_MIKSIS;
+  return (s->scheme == ODE_RK4 && s->prec == ODE_FP64 && forced && s->pr.td_mode == kTdKeep)
+             ? kForcingTable : 0;
+}
+
+// Blocks per SM and block size for a launch of `fn` with `smem` bytes of
+// dynamic shared memory.
+int launch_shape(ode_solver* s, const void* fn, int* block, int* blocks_per_sm, int* sms, size_t smem = 0) {
   int bs = s->block_size;
   if (bs <= 0) bs = 128;
   CK_CUDA(s, cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, s->device));
-  CK_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, bs, 0));
+  CK_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, bs, smem));
   if (*blocks_per_sm < 1)
     return fail(s, ODE_ERR_UNSUPPORTED, "kernel cannot be resident with the requested block size");
   *block = bs;
@@ -369,12 +386,15 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.queue_head = s->d_queue;
   a.queue_mode = s->persistent;
   a.queue_stride = queue_stride_for(s->N);
+  a.spt = s->persistent ? 1 : s->spt;
+  a.tab_cap = forcing_table_entries(s);
+  const size_t smem = (size_t)a.tab_cap * sizeof(double2);
   a.flags = (int*)((char*)s->d_queue + 64);
   a.time_limit_ns = (long long)(s->time_limit_s * 1e9);
   a.pr = s->pr;
   finish_props(a.pr);
   int block, bps, sms;
-  if (int rc = launch_shape(s, fn, &block, &bps, &sms)) return rc;
+  if (int rc = launch_shape(s, fn, &block, &bps, &sms, smem)) return rc;
   long long grid;
   if (s->persistent) {
     CK_CUDA(s, cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned int), st));
@@ -382,11 +402,26 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
     long long need = (s->N + block - 1) / block;
     if (grid > need) grid = need;
   } else {
-    grid = (s->N + block - 1) / block;
+    const long long per_block = (long long)block * a.spt;
+    grid = (s->N + per_block - 1) / per_block;
   }
   if (grid < 1) grid = 1;
   void* args[] = {&a};
-  CK_CUDA(s, cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, 0, st));
+  CK_CUDA(s, cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, smem, st));
+  return ODE_OK;
+}
+
+// n_slices slices in launches of at most slices_per_launch slices each (0 =
+// one launch).  Every launch stores each system's full state and time
+// domain, so the split does not change any result; records of global slice
+// g >= n_transient go to index g - n_transient (a launch starting at slice c0
+// skips n_transient - c0 slices, which may be negative).
+int run_slices(ode_solver* s, double h0, int n_slices, int n_transient, double* records, void* stream) {
+  const int L = s->slices_per_launch > 0 ? s->slices_per_launch : n_slices;
+  for (int c0 = 0; c0 < n_slices; c0 += L) {
+    const int n = std::min(L, n_slices - c0);
+    if (int rc = integrate(s, h0, n, n_transient - c0, records, stream)) return rc;
+  }
   return ODE_OK;
 }
 
@@ -578,6 +613,16 @@ int ode_set_launch(ode_solver* s, int block_size, int persistent) {
   return ODE_OK;
 }
 
+int ode_set_schedule(ode_solver* s, int systems_per_thread, int slices_per_launch) {
+  if (check_solver(s)) return ODE_ERR_INVALID_ARG;
+  if (systems_per_thread < 1 || systems_per_thread > 64)
+    return fail(s, ODE_ERR_INVALID_ARG, "systems_per_thread must be in [1, 64]");
+  if (slices_per_launch < 0) return fail(s, ODE_ERR_INVALID_ARG, "slices_per_launch must be >= 0");
+  s->spt = systems_per_thread;
+  s->slices_per_launch = slices_per_launch;
+  return ODE_OK;
+}
+
 int ode_linear_set(ode_solver* s, int start_obj, int start_pool, int pool_size, int count,
                    const double* td, const double* y, const double* p, const double* acc,
                    int copy_mode, int ptr_kind, void* stream) {
@@ -644,7 +689,7 @@ int ode_run_periods(ode_solver* s, double h0, int n_transient, int n_record, dou
       dev_rec = s->d_records;
     }
   }
-  if (int rc = integrate(s, h0, n_slices, n_transient, dev_rec, stream)) return rc;
+  if (int rc = run_slices(s, h0, n_slices, n_transient, dev_rec, stream)) return rc;
   if (records != nullptr && n_record > 0 && ptr_kind == ODE_PTR_HOST) {
     CK_CUDA(s, cudaMemcpyAsync(records, dev_rec, rec_doubles * sizeof(double),
                                cudaMemcpyDeviceToHost, st));
@@ -690,11 +735,13 @@ int ode_reset_counters(ode_solver* s, void* stream) {
 const char* ode_last_error(const ode_solver* s) { return s ? s->err.c_str() : g_err.c_str(); }
 
 int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* block_size,
-                 int* persistent, double* trial_ms) {
+                 int* persistent, int* systems_per_thread, int* slices_per_launch, double* trial_ms) {
   if (check_solver(s)) return ODE_ERR_INVALID_ARG;
   if (!(h0 > 0.0) || !isfinite(h0)) return fail(s, ODE_ERR_INVALID_ARG, "h0 must be finite and > 0");
   if (n_slices < 1 || n_slices > 1000000) return fail(s, ODE_ERR_INVALID_ARG, "n_slices out of range");
   static const int kBlocks[6] = {64, 96, 128, 160, 192, 256};
+  // launch forms: (persistent, systems per thread)
+  static const int kForms[4][2] = {{0, 1}, {0, 2}, {1, 1}, {2, 1}};
   DeviceGuard g(s->device);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t N = (size_t)s->N;
@@ -721,37 +768,70 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
     return cudaSuccess;
   };
   cudaError_t e = copy_all(true);
-  const int old_block = s->block_size, old_pers = s->persistent;
+  const int old_block = s->block_size, old_pers = s->persistent, old_spt = s->spt,
+            old_spl = s->slices_per_launch;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = ODE_OK;
+  // one timed trial of the current shape; ms < 0 when it was not run
+  auto trial = [&](float* ms) -> bool {
+    *ms = -1.f;
+    if ((e = copy_all(false)) != cudaSuccess) return false;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return false;
+    if ((rc = run_slices(s, h0, n_slices, n_slices, nullptr, stream)) != ODE_OK) return false;
+    if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return false;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return false;
+    return (e = cudaEventElapsedTime(ms, e0, e1)) == cudaSuccess;
+  };
   double best = 1e300;
-  int best_b = 128, best_p = 1, rc = ODE_OK;
-  int max_threads = 1024;
-  for (int pers = 0; pers < 3 && e == cudaSuccess && rc == ODE_OK; pers++) {
+  int best_b = 128, best_p = 1, best_spt = 1, best_spl = 0;
+  for (int f = 0; f < 4 && e == cudaSuccess && rc == ODE_OK; f++) {
+    const int pers = kForms[f][0], spt = kForms[f][1];
     const void* fn = kernel_for(s->model, s->scheme, s->prec, pers ? 1 : 0);
+    int max_threads = 1024;
     cudaFuncAttributes at;
     if (fn && cudaFuncGetAttributes(&at, fn) == cudaSuccess) max_threads = at.maxThreadsPerBlock;
-    for (int k = 0; k < 6 && e == cudaSuccess; k++) {
-      if (trial_ms) trial_ms[pers * 6 + k] = -1.0;
+    for (int k = 0; k < 6 && e == cudaSuccess && rc == ODE_OK; k++) {
+      if (trial_ms) trial_ms[f * 6 + k] = -1.0;
       if (!fn || kBlocks[k] > max_threads) continue;
       int bps = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlocks[k], 0) != cudaSuccess || bps < 1)
         continue;
       s->block_size = kBlocks[k];
       s->persistent = pers;
-      if ((e = copy_all(false)) != cudaSuccess) break;
-      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-      if ((rc = integrate(s, h0, n_slices, n_slices, nullptr, stream)) != ODE_OK) break;
-      if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.f;
-      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
-      if (trial_ms) trial_ms[pers * 6 + k] = ms;
+      s->spt = spt;
+      s->slices_per_launch = 0;
+      float ms;
+      if (!trial(&ms)) break;
+      if (trial_ms) trial_ms[f * 6 + k] = ms;
       if (ms < best) {
         best = ms;
         best_b = kBlocks[k];
         best_p = pers;
+        best_spt = spt;
+      }
+    }
+  }
+  // slices per launch for the best shape: one slice per launch, half of the
+  // trial's slices per launch, all in one launch (the time measured above)
+  if (trial_ms)
+    for (int k = 0; k < 3; k++) trial_ms[24 + k] = -1.0;
+  if (e == cudaSuccess && rc == ODE_OK) {
+    if (trial_ms) trial_ms[26] = best;
+    const int cand[2] = {1, (n_slices + 1) / 2};
+    for (int k = 0; k < 2 && e == cudaSuccess && rc == ODE_OK; k++) {
+      if (cand[k] >= n_slices || (k == 1 && cand[1] == cand[0])) continue;
+      s->block_size = best_b;
+      s->persistent = best_p;
+      s->spt = best_spt;
+      s->slices_per_launch = cand[k];
+      float ms;
+      if (!trial(&ms)) break;
+      if (trial_ms) trial_ms[24 + k] = ms;
+      if (ms < best) {
+        best = ms;
+        best_spl = cand[k];
       }
     }
   }
@@ -763,12 +843,18 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
   if (rc != ODE_OK || e != cudaSuccess) {
     s->block_size = old_block;
     s->persistent = old_pers;
+    s->spt = old_spt;
+    s->slices_per_launch = old_spl;
     return rc != ODE_OK ? rc : cuda_fail(s, e, "ode_autotune");
   }
   s->block_size = best_b;
   s->persistent = best_p;
+  s->spt = best_spt;
+  s->slices_per_launch = best_spl;
   if (block_size) *block_size = best_b;
   if (persistent) *persistent = best_p;
+  if (systems_per_thread) *systems_per_thread = best_spt;
+  if (slices_per_launch) *slices_per_launch = best_spl;
   return check_watchdog(s, st);
 }
 

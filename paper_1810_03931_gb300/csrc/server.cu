@@ -1,33 +1,37 @@
-// server.cu -- continuous-batching request loop for parameter-sweep requests.
+// server.cu -- continuous-batching request loop for parameter-sweep requests,
+// built on the resident serving kernel of serve.cuh.
 //
-// Each model has a resident pool of system slots in HBM (its size chosen by
-// the caller within the server's HBM budget).  A request -- n systems of one
-// model, each integrated for a number of periods (slices) -- is admitted when
-// a contiguous range of free slots exists; its inputs are copied into the
-// range and its state stays resident there until its horizon is done.  An
-// admitted request advances in chunks of slices: each chunk is one launch of
-// the integrator over the request's slot range (captured once as a CUDA graph
-// at admission and replayed), on one of the server's streams.  The chunk
-// length is fixed (`slice_periods`) or tuned per request (slice_periods = 0):
-// each chunk is timed with events and the next one is sized so that a chunk
-// takes about kChunkTargetMs -- long enough to amortise the launch and the
-// host's polling, short enough that a finished request is noticed soon.
-// Chunks of different requests and models run concurrently on the device; a
-// request's next chunk is launched as soon as its previous chunk completes,
-// so requests never wait for each other's slow systems.  A finished request is
-// copied out asynchronously on its stream; its slots return to the free list
-// only once that copy has completed (its event has fired), because the next
-// occupant of the range may be admitted on another stream, whose copies and
-// launches stream order would not keep behind the pending copy.
+// Each served model has a pool of system slots in HBM (capacity chosen by the
+// caller within the server's HBM budget: admission by footprint) and, while
+// it has work, one or more resident instances of its serving kernel.  A
+// request -- n systems of one model, each integrated over n_periods slices --
+// waits (FIFO per model) until a contiguous range of n free slots exists.
+// Admission copies its inputs, slice budgets and request-table entry into the
+// range; its slot indices are then published to the model's ring, from which
+// the kernel's threads take systems the moment they free up.  A thread runs a
+// system for its whole horizon (or for slice_periods slices, after which the
+// system goes back through the host to the ring: time slicing), stores it
+// and counts it in its request's done counter.  When a request's count
+// reaches n, its results are copied out (pinned D2H) and, once that copy has
+// completed, its slots return to the free list.  Requests that arrive while
+// others run are merged into the same launch: there is one launch per model
+// and residency, not per request.
 //
-// Each system's arithmetic does not depend on its slot, its neighbours or the
-// chunk boundaries (every slice restarts from its own state), so a request's
-// results are the same alone and in any mix.
+// The host side never blocks: ode_server_progress takes one asynchronous
+// snapshot of the done counters and the yield list per call, publishes ring
+// entries, starts kernel instances and copies results out.  Blocks are split
+// between models with work in equal shares; a model that gets work while the
+// others hold the GPU has them stop at their next slice boundary (their
+// systems come back through the yield list) and all are relaunched with the
+// new split.  Every system's arithmetic is that of ode_run_periods, so a
+// request's results are the same alone and in any mix.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <deque>
 #include <map>
 #include <new>
@@ -46,42 +50,73 @@ double now_s() {
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-// One-thread-per-system kernel (no work queue) of a model.
-const void* kernel_of(int model, int scheme, int prec) { return kernel_for(model, scheme, prec, 0); }
-
-__global__ void fill_int_kernel(int* p, int n, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
-}
-
 enum ReqState { kWaiting = 0, kRunning = 1, kDone = 2 };
+
+constexpr int kMaxReq = 4096;         // request-table entries per model (done counters)
+constexpr int kTailWords = 256;       // pinned words for ring-tail publishes
+constexpr int kThreads = 128;         // threads per block of the serving kernel
+constexpr long long kIdleNs = 2000000;  // a warp without work exits after 2 ms
+
+// Pinned host buffers are recycled by size class instead of freed:
+// cudaFreeHost waits for the device, which would stall every request's result
+// behind the resident kernels.  Buffers go back to the server's cache and are
+// released only when the server is destroyed.
+struct PinnedCache {
+  std::map<size_t, std::vector<void*>> free_lists;
+  static size_t klass(size_t bytes) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  cudaError_t get(void** p, size_t bytes) {
+    auto& fl = free_lists[klass(bytes)];
+    if (!fl.empty()) {
+      *p = fl.back();
+      fl.pop_back();
+      return cudaSuccess;
+    }
+    return cudaMallocHost(p, klass(bytes));
+  }
+  void put(void* p, size_t bytes) {
+    if (p) free_lists[klass(bytes)].push_back(p);
+  }
+  void release() {
+    for (auto& kv : free_lists)
+      for (void* p : kv.second) cudaFreeHost(p);
+    free_lists.clear();
+  }
+};
 
 struct Request {
   long long ticket = 0;
   int model = 0;
   int n = 0;
   int periods = 0;
-  int scheduled = 0;  // periods enqueued in chunks so far
-  int chunk = 1;      // slices in the next chunk
-  int graph_chunk = 0;  // slices the instantiated graph runs
-  cudaGraph_t graph_def = nullptr;  // the captured graph (kept: owns the node)
-  cudaGraphNode_t node = nullptr;    // its kernel node
-  cudaKernelNodeParams kp;           // the node's launch (function, grid, block)
-  KArgs args;                        // its arguments (n_slices updated per chunk)
-  int off = -1;       // first slot
+  int off = -1;            // first slot
+  int tix = -1;            // request-table entry
+  unsigned int base = 0;   // done counter value when admitted
+  int fresh = 0;           // systems admitted but not yet published to the ring
+  std::deque<int> yielded; // its slots handed back by the kernel, to publish again
+  bool in_feed = false;
   int state = kWaiting;
   bool harvesting = false;
   double t_submit = 0, t_done = 0;
-  // pinned host buffers: inputs [2 + n_sys + P][n], outputs
+  // pinned host buffers: inputs [2 + n_sys + P][n], budgets and table
+  // entries [2][n] (int), zero counters [2][n] (long long), outputs
   double* h_in = nullptr;
+  int* h_meta = nullptr;
+  long long* h_zero = nullptr;
   double* h_out = nullptr;  // td [2][n], y [n_sys][n], acc [A][n]
   int* h_status = nullptr;
   long long* h_acc_steps = nullptr;
-  cudaEvent_t done_ev = nullptr;   // results copied out
-  cudaEvent_t chunk_ev = nullptr;  // last chunk finished
-  cudaEvent_t start_ev = nullptr;  // last chunk started (tuned chunk length)
-  cudaStream_t stream = nullptr;   // borrowed from the server's stream set
-  cudaGraphExec_t graph = nullptr; // one chunk of this request
-  bool chunk_inflight = false;
+  cudaEvent_t done_ev = nullptr;  // results copied out
+  size_t b_in = 0, b_meta = 0, b_zero = 0, b_out = 0, b_status = 0, b_steps = 0;  // buffer sizes
+};
+
+struct Instance {
+  cudaEvent_t ev = nullptr;  // completion
+  int blocks = 0;
+  bool live = false;
 };
 
 struct Pool {
@@ -92,31 +127,71 @@ struct Pool {
   double h0 = 0;
   Props pr;
   double time_limit_s = 600;
+  const void* fn = nullptr;
+  int bps = 0;  // resident blocks per SM of the serving kernel
+  // device
   double *td = nullptr, *y = nullptr, *p = nullptr, *acc = nullptr;
-  int *status = nullptr, *ecnt = nullptr, *left = nullptr;
+  int *status = nullptr, *ecnt = nullptr, *left = nullptr, *owner = nullptr;
   long long *nacc = nullptr, *nrej = nullptr;
-  unsigned char* head = nullptr;  // watchdog flag
+  unsigned int* ring = nullptr;
+  unsigned int* ctl = nullptr;
+  unsigned long long* yl = nullptr;
+  unsigned int* done = nullptr;
+  unsigned int ring_cap = 0, yl_cap = 0;
+  // host
   std::map<int, int> free_ranges;  // offset -> length
+  std::vector<int> free_tix;
+  std::vector<unsigned int> tix_base;  // done counter value after the last occupant
   std::deque<Request*> waiting;
-  std::vector<Request*> running;
+  std::vector<Request*> running;       // admitted, not finished
+  std::deque<Request*> feed;           // admitted requests with systems to publish (round robin)
+  std::vector<Request*> slot_req;      // request holding each slot
+  unsigned int tail = 0;               // ring entries published
+  unsigned int yl_read = 0;            // yield-list entries taken back
+  unsigned int* h_ring = nullptr;      // pinned staging of ring entries [ring_cap]
+  unsigned int* h_tail = nullptr;      // pinned words for tail publishes [kTailWords]
+  cudaEvent_t tail_ev[kTailWords] = {};
+  int tail_next = 0;
+  unsigned int* h_ctl = nullptr;       // pinned snapshot of the control block
+  unsigned int* h_done = nullptr;      // pinned snapshot of the done counters
+  unsigned long long* h_yl = nullptr;  // pinned snapshot of the yield list [yl_cap]
+  unsigned int snap_yl_lo = 0, snap_yl_hi = 0;  // yield-list range in the snapshot
+  unsigned int* h_flag = nullptr;      // pinned stop-flag words [2]: 0 and 1
+  cudaEvent_t snap_ev = nullptr;
+  bool snap_inflight = false;
+  bool snap_valid = false;
+  unsigned int known_yield_tail = 0;   // from the last snapshot
+  cudaStream_t cstream = nullptr;      // the server's copy stream (shared by the pools)
+  cudaStream_t kstream = nullptr;      // the serving kernel's stream
+  Instance inst;                       // the resident instance (at most one)
+  bool stopping = false;               // stop flag raised for a rebalance
+  int target_blocks = 0;
+  long long unfinished = 0;            // systems admitted and not yet counted done
   size_t bytes = 0;
-  long long chunks = 0;
+  long long launches = 0;   // serving-kernel instances started
+  long long stops = 0;      // stop requests (rebalancing)
+  long long yielded = 0;    // systems taken back from the yield list
+  long long snapshots = 0;  // snapshots read
+  long long published = 0;  // ring entries published
+  long long finished = 0;   // requests copied out
+  unsigned int flags = 0;   // watchdog / bounds flags seen
 };
-
-constexpr int kStreams = 32;
-constexpr double kChunkTargetMs = 25.0;  // tuned chunks: aimed duration
-constexpr int kMaxChunk = 4096;
 
 }  // namespace
 
 struct ode_server {
   int device = 0;
-  int slice_periods = 1;
+  int slice_periods = 0;
+  int sms = 0;
+  // Few streams on purpose: streams share the device's hardware work queues,
+  // and a copy queued behind a resident kernel in the same queue would wait
+  // for the kernel to end.  One copy stream for all pools and one kernel
+  // stream per pool stay within the default number of queues.
+  cudaStream_t cstream = nullptr;
   long long budget = 0;
   long long used = 0;
   Pool pools[kNumModels];
-  cudaStream_t streams[kStreams] = {};
-  int next_stream = 0;
+  PinnedCache pinned;
   std::map<long long, Request*> reqs;
   long long next_ticket = 1;
   std::string err;
@@ -140,8 +215,12 @@ int scuda(ode_server* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return scuda((s), e_, #call);    \
   } while (0)
 
+// device bytes per slot: time domain, state, parameters, accessories, status,
+// event counters, slice budget, owner, two step counters, a ring entry and a
+// yield-list entry
 size_t per_system_bytes(int n, int P, int A, int E) {
-  return sizeof(double) * (2 + n + P + A) + sizeof(int) * (2 + E) + 2 * sizeof(long long);
+  return sizeof(double) * (2 + n + P + A) + sizeof(int) * (3 + E) + 2 * sizeof(long long) +
+         sizeof(unsigned int) + sizeof(unsigned long long);
 }
 
 // first-fit range allocator over the pool's slots
@@ -173,149 +252,151 @@ void give_range(Pool& pl, int off, int len) {
   }
 }
 
-// Capture one chunk of a request: slice_periods slices (at most the request's
-// remaining ones, via the per-slot counts) of its slot range.
-int build_request_graph(ode_server* s, Pool& pl, Request* r) {
-  const void* fn = kernel_of(pl.model, pl.scheme, pl.prec);
-  const size_t off = (size_t)r->off;
-  KArgs a;
-  memset(&a, 0, sizeof(a));
-  a.N = r->n;
-  a.ld = pl.cap;
-  a.td = pl.td + off;
-  a.y = pl.y + off;
-  a.p = pl.p + off;
-  a.acc = pl.acc + off;
-  a.status = pl.status + off;
-  a.ecnt = pl.ecnt + off;
-  a.nacc = pl.nacc + off;
-  a.nrej = pl.nrej + off;
-  a.records = nullptr;
-  a.n_slices = r->chunk;
-  a.n_skip = r->chunk;
-  a.h0 = pl.h0;
-  a.slices_left = pl.left + off;
-  a.queue_head = nullptr;
-  a.queue_stride = 1u;
-  a.flags = (int*)(pl.head + 64);
-  a.time_limit_ns = (long long)(pl.time_limit_s * 1e9);
-  a.pr = pl.pr;
-  const int block = 64;  // one thread per system, no work queue
-  const unsigned grid = (unsigned)((r->n + block - 1) / block);
-  cudaGraph_t g = nullptr;
-  SCK(s, cudaGraphCreate(&g, 0));
-  void* args[] = {&a};
-  cudaKernelNodeParams kp;
-  memset(&kp, 0, sizeof(kp));
-  kp.func = (void*)fn;
-  kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(block);
-  kp.sharedMemBytes = 0;
-  kp.kernelParams = args;
-  cudaError_t e = cudaGraphAddKernelNode(&r->node, g, nullptr, 0, &kp);
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&r->graph, g, 0);
-  r->graph_def = g;  // kept with the request: its node is updated per chunk
-  if (e != cudaSuccess) return scuda(s, e, "chunk graph");
-  r->kp = kp;
-  r->kp.kernelParams = nullptr;
-  r->args = a;
-  r->graph_chunk = r->chunk;
-  return ODE_OK;
-}
-
-void free_request(Request* r) {
-  if (r->h_in) cudaFreeHost(r->h_in);
-  if (r->h_out) cudaFreeHost(r->h_out);
-  if (r->h_status) cudaFreeHost(r->h_status);
-  if (r->h_acc_steps) cudaFreeHost(r->h_acc_steps);
+void free_request(PinnedCache& pc, Request* r) {
+  pc.put(r->h_in, r->b_in);
+  pc.put(r->h_meta, r->b_meta);
+  pc.put(r->h_zero, r->b_zero);
+  pc.put(r->h_out, r->b_out);
+  pc.put(r->h_status, r->b_status);
+  pc.put(r->h_acc_steps, r->b_steps);
   if (r->done_ev) cudaEventDestroy(r->done_ev);
-  if (r->chunk_ev) cudaEventDestroy(r->chunk_ev);
-  if (r->start_ev) cudaEventDestroy(r->start_ev);
-  if (r->graph) cudaGraphExecDestroy(r->graph);
-  if (r->graph_def) cudaGraphDestroy(r->graph_def);
   delete r;
 }
 
-// Copy a request's inputs into its slot range and arm its slice count.
-int launch_chunk(ode_server* s, Pool& pl, Request* r) {
-  if (r->chunk != r->graph_chunk) {
-    // same node, new slice count: update the executable graph in place
-    r->args.n_slices = r->chunk;
-    r->args.n_skip = r->chunk;
-    void* args[] = {&r->args};
-    cudaKernelNodeParams kp = r->kp;
-    kp.kernelParams = args;
-    SCK(s, cudaGraphExecKernelNodeSetParams(r->graph, r->node, &kp));
-    r->graph_chunk = r->chunk;
-  }
-  if (s->slice_periods == 0) SCK(s, cudaEventRecord(r->start_ev, r->stream));
-  SCK(s, cudaGraphLaunch(r->graph, r->stream));
-  SCK(s, cudaEventRecord(r->chunk_ev, r->stream));
-  r->chunk_inflight = true;
-  r->scheduled += r->chunk;
-  pl.chunks++;
-  return ODE_OK;
-}
+}  // namespace
 
-// Tuned chunk length: scale the last chunk's slice count towards the target
-// duration (at most 4x up or down per step).
-void retune_chunk(Request* r) {
-  float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, r->start_ev, r->chunk_ev) != cudaSuccess || !(ms > 0.f)) return;
-  double f = kChunkTargetMs / (double)ms;
-  f = f > 4.0 ? 4.0 : (f < 0.25 ? 0.25 : f);
-  int c = (int)floor(r->chunk * f + 0.5);
-  c = c < 1 ? 1 : (c > kMaxChunk ? kMaxChunk : c);
-  r->chunk = c;
-}
+namespace {
 
+// Copy a request's inputs, slice budgets, request-table entry and zero step
+// counters into its slot range (on the pool's copy stream).
 int admit(ode_server* s, Pool& pl, Request* r) {
   const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
   const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
+  const size_t irow = n * sizeof(int), ipitch = cap * sizeof(int);
+  cudaStream_t st = s->cstream;
+  r->tix = pl.free_tix.back();
+  pl.free_tix.pop_back();
+  r->base = pl.tix_base[r->tix];
+  for (size_t i = 0; i < n; i++) {
+    r->h_meta[i] = r->periods;        // slice budget
+    r->h_meta[n + i] = r->tix;        // request-table entry
+  }
   const double* in = r->h_in;
-  r->stream = s->streams[s->next_stream];
-  s->next_stream = (s->next_stream + 1) % kStreams;
-  cudaStream_t st = r->stream;
   SCK(s, cudaMemcpy2DAsync(pl.td + r->off, pitch, in, row, row, 2, cudaMemcpyHostToDevice, st));
   SCK(s, cudaMemcpy2DAsync(pl.y + r->off, pitch, in + 2 * n, row, row, pl.n, cudaMemcpyHostToDevice, st));
   SCK(s, cudaMemcpy2DAsync(pl.p + r->off, pitch, in + (2 + pl.n) * n, row, row, pl.P,
                            cudaMemcpyHostToDevice, st));
-  SCK(s, cudaMemsetAsync(pl.nacc + r->off, 0, n * sizeof(long long), st));
-  SCK(s, cudaMemsetAsync(pl.nrej + r->off, 0, n * sizeof(long long), st));
-  fill_int_kernel<<<(r->n + 255) / 256 < 1024 ? (r->n + 255) / 256 : 1024, 256, 0, st>>>(
-      pl.left + r->off, r->n, r->periods);
-  SCK(s, cudaGetLastError());
-  r->chunk = s->slice_periods > 0 ? s->slice_periods : 1;
-  if (int rc = build_request_graph(s, pl, r)) return rc;
+  SCK(s, cudaMemcpyAsync(pl.left + r->off, r->h_meta, irow, cudaMemcpyHostToDevice, st));
+  SCK(s, cudaMemcpyAsync(pl.owner + r->off, r->h_meta + n, irow, cudaMemcpyHostToDevice, st));
+  SCK(s, cudaMemcpyAsync(pl.nacc + r->off, r->h_zero, n * sizeof(long long), cudaMemcpyHostToDevice, st));
+  SCK(s, cudaMemcpyAsync(pl.nrej + r->off, r->h_zero + n, n * sizeof(long long), cudaMemcpyHostToDevice, st));
+  (void)ipitch;
   r->state = kRunning;
-  r->scheduled = 0;
+  r->fresh = r->n;
+  for (int i = 0; i < r->n; i++) pl.slot_req[r->off + i] = r;
   pl.running.push_back(r);
-  return launch_chunk(s, pl, r);
+  r->in_feed = true;
+  pl.feed.push_back(r);
+  pl.unfinished += r->n;
+  return ODE_OK;
 }
 
-// Copy a finished request's results out (after its last chunk, in stream order).
+// From the last snapshot: ring entries published but not yet taken, and the
+// threads of the running instance without a system (claimed entries minus
+// systems finished -- the sum of the monotone done counters -- minus systems
+// handed back).
+unsigned int ring_outstanding(const Pool& pl) {
+  const unsigned int head = pl.snap_valid ? pl.h_ctl[kCtlRingHead] : 0u;
+  return pl.tail - head;
+}
+
+long long idle_threads(const Pool& pl) {
+  const long long lanes = pl.inst.live ? (long long)pl.inst.blocks * kThreads : 0;
+  if (!pl.snap_valid) return lanes;
+  unsigned int done = 0;
+  for (int t = 0; t < kMaxReq; t++) done += pl.h_done[t];
+  const unsigned int in_flight = pl.h_ctl[kCtlRingHead] - done - pl.h_ctl[kCtlYieldTail];
+  return std::max(0LL, lanes - (long long)in_flight);
+}
+
+// Publish slots to the ring, round robin over the requests that have systems
+// to run (their yielded systems first, then fresh ones), in chunks of
+// kChunk, and only as many as the running instance has idle threads plus a
+// margin: a request that arrives later is then never queued behind the whole
+// of an earlier one.  Entries are staged in pinned memory at their ring
+// positions and copied, then the new tail is copied from a pinned word of
+// its own (a word is reused only after its copy has completed).
+int publish(ode_server* s, Pool& pl) {
+  const int w = pl.tail_next;
+  if (pl.tail_ev[w]) {
+    cudaError_t q = cudaEventQuery(pl.tail_ev[w]);
+    if (q == cudaErrorNotReady) return ODE_OK;  // try again on the next pass
+    if (q != cudaSuccess) return scuda(s, q, "ring tail copy");
+  }
+  constexpr long long kMargin = 512;
+  constexpr int kChunk = 256;
+  long long room = idle_threads(pl) + kMargin - (long long)ring_outstanding(pl);
+  const unsigned int first = pl.tail;
+  unsigned int k = 0;
+  while (room > 0 && !pl.feed.empty()) {
+    Request* r = pl.feed.front();
+    pl.feed.pop_front();
+    int take = 0;
+    while (take < kChunk && room > 0 && !r->yielded.empty()) {
+      pl.h_ring[(first + k) % pl.ring_cap] = (unsigned int)r->yielded.front();
+      r->yielded.pop_front();
+      k++, take++, room--;
+    }
+    while (take < kChunk && room > 0 && r->fresh > 0) {
+      pl.h_ring[(first + k) % pl.ring_cap] = (unsigned int)(r->off + (r->n - r->fresh));
+      r->fresh--;
+      k++, take++, room--;
+    }
+    r->in_feed = r->fresh > 0 || !r->yielded.empty();
+    if (r->in_feed) pl.feed.push_back(r);
+  }
+  if (k == 0) return ODE_OK;
+  // one or two contiguous segments of the ring
+  const unsigned int a0 = first % pl.ring_cap;
+  const unsigned int n0 = std::min(k, pl.ring_cap - a0);
+  SCK(s, cudaMemcpyAsync(pl.ring + a0, pl.h_ring + a0, n0 * sizeof(unsigned int), cudaMemcpyHostToDevice,
+                         s->cstream));
+  if (n0 < k)
+    SCK(s, cudaMemcpyAsync(pl.ring, pl.h_ring, (k - n0) * sizeof(unsigned int), cudaMemcpyHostToDevice,
+                           s->cstream));
+  pl.tail = first + k;
+  pl.published += k;
+  pl.h_tail[w] = pl.tail;
+  SCK(s, cudaMemcpyAsync(pl.ctl + kCtlRingTail, pl.h_tail + w, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                         s->cstream));
+  SCK(s, cudaEventRecord(pl.tail_ev[w], s->cstream));
+  pl.tail_next = (w + 1) % kTailWords;
+  return ODE_OK;
+}
+
+// Copy a finished request's results out (pinned D2H on the copy stream).
 int harvest(ode_server* s, Pool& pl, Request* r) {
   const size_t n = (size_t)r->n, cap = (size_t)pl.cap;
   const size_t row = n * sizeof(double), pitch = cap * sizeof(double);
   double* out = r->h_out;
-  cudaStream_t stream = r->stream;
-  SCK(s, cudaMemcpy2DAsync(out, row, pl.td + r->off, pitch, row, 2, cudaMemcpyDeviceToHost, stream));
-  SCK(s, cudaMemcpy2DAsync(out + 2 * n, row, pl.y + r->off, pitch, row, pl.n, cudaMemcpyDeviceToHost,
-                           stream));
+  cudaStream_t st = s->cstream;
+  SCK(s, cudaMemcpy2DAsync(out, row, pl.td + r->off, pitch, row, 2, cudaMemcpyDeviceToHost, st));
+  SCK(s, cudaMemcpy2DAsync(out + 2 * n, row, pl.y + r->off, pitch, row, pl.n, cudaMemcpyDeviceToHost, st));
   SCK(s, cudaMemcpy2DAsync(out + (2 + pl.n) * n, row, pl.acc + r->off, pitch, row, pl.A,
-                           cudaMemcpyDeviceToHost, stream));
-  SCK(s, cudaMemcpyAsync(r->h_status, pl.status + r->off, n * sizeof(int), cudaMemcpyDeviceToHost,
-                         stream));
-  SCK(s, cudaMemcpyAsync(r->h_acc_steps, pl.nacc + r->off, n * sizeof(long long),
-                         cudaMemcpyDeviceToHost, stream));
-  SCK(s, cudaEventRecord(r->done_ev, stream));
+                           cudaMemcpyDeviceToHost, st));
+  SCK(s, cudaMemcpyAsync(r->h_status, pl.status + r->off, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SCK(s, cudaMemcpyAsync(r->h_acc_steps, pl.nacc + r->off, n * sizeof(long long), cudaMemcpyDeviceToHost,
+                         st));
+  SCK(s, cudaEventRecord(r->done_ev, st));
   r->harvesting = true;
-  // the slot range is released in release_harvested(), after done_ev
+  pl.unfinished -= r->n;
+  pl.finished++;
   return ODE_OK;
 }
 
 // Requests whose results have arrived: mark them done and only now return
-// their slot ranges to the pool's free list.
+// their slots and request-table entries (the copy out has completed, so a
+// later admission into the same range cannot overwrite results in flight).
 int release_harvested(ode_server* s) {
   for (auto& kv : s->reqs) {
     Request* r = kv.second;
@@ -325,7 +406,210 @@ int release_harvested(ode_server* s) {
     if (q != cudaSuccess) return scuda(s, q, "harvest");
     r->state = kDone;
     r->t_done = now_s();
-    give_range(s->pools[r->model], r->off, r->n);
+    Pool& pl = s->pools[r->model];
+    give_range(pl, r->off, r->n);
+    pl.tix_base[r->tix] = r->base + (unsigned int)r->n;
+    pl.free_tix.push_back(r->tix);
+  }
+  return ODE_OK;
+}
+
+// Start an asynchronous snapshot of the control block, the done counters and
+// the yield-list entries reserved up to the previous snapshot.
+int start_snapshot(ode_server* s, Pool& pl) {
+  cudaStream_t st = s->cstream;
+  SCK(s, cudaMemcpyAsync(pl.h_ctl, pl.ctl, kCtlWords * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  SCK(s, cudaMemcpyAsync(pl.h_done, pl.done, kMaxReq * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  pl.snap_yl_lo = pl.yl_read;
+  pl.snap_yl_hi = pl.known_yield_tail;
+  const unsigned int k = pl.snap_yl_hi - pl.snap_yl_lo;
+  if (k > 0) {
+    const unsigned int a0 = pl.snap_yl_lo % pl.yl_cap;
+    const unsigned int n0 = std::min(k, pl.yl_cap - a0);
+    SCK(s, cudaMemcpyAsync(pl.h_yl + a0, pl.yl + a0, n0 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           st));
+    if (n0 < k)
+      SCK(s, cudaMemcpyAsync(pl.h_yl, pl.yl, (k - n0) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             st));
+  }
+  SCK(s, cudaEventRecord(pl.snap_ev, st));
+  pl.snap_inflight = true;
+  return ODE_OK;
+}
+
+// A completed snapshot: take back yielded slots, copy out finished requests.
+int take_snapshot(ode_server* s, Pool& pl) {
+  pl.snap_inflight = false;
+  pl.snap_valid = true;
+  pl.snapshots++;
+  pl.flags |= pl.h_ctl[kCtlFlags];
+  pl.known_yield_tail = pl.h_ctl[kCtlYieldTail];
+  while (pl.yl_read != pl.snap_yl_hi) {
+    const unsigned int pos = pl.yl_read;
+    const unsigned long long e = pl.h_yl[pos % pl.yl_cap];
+    if ((unsigned int)(e >> 32) != pos / pl.yl_cap + 1u) break;  // reserved, not yet written
+    const int slot = (int)(e & 0xffffffffu);
+    pl.yl_read++;
+    Request* r = (slot >= 0 && slot < pl.cap) ? pl.slot_req[slot] : nullptr;
+    if (r && r->state == kRunning && !r->harvesting) {
+      r->yielded.push_back(slot);
+      if (!r->in_feed) {
+        r->in_feed = true;
+        pl.feed.push_back(r);
+      }
+    }
+    pl.yielded++;
+  }
+  std::vector<Request*> still;
+  for (Request* r : pl.running) {
+    const unsigned int cnt = pl.h_done[r->tix] - r->base;
+    if (cnt >= (unsigned int)r->n) {
+      if (int rc = harvest(s, pl, r)) return rc;
+    } else {
+      still.push_back(r);
+    }
+  }
+  pl.running.swap(still);
+  return ODE_OK;
+}
+
+}  // namespace
+
+namespace {
+
+double share_of(const Pool& pl, int blocks, int sms) {
+  return pl.bps > 0 ? (double)blocks / ((double)pl.bps * sms) : 0.0;
+}
+
+int live_blocks(const Pool& pl) { return pl.inst.live ? pl.inst.blocks : 0; }
+
+// Write the stop flag of a pool (0 or 1) on its copy stream.
+int set_stop(ode_server* s, Pool& pl, int v) {
+  SCK(s, cudaMemcpyAsync(pl.ctl + kCtlStop, pl.h_flag + (v ? 1 : 0), sizeof(unsigned int),
+                         cudaMemcpyHostToDevice, s->cstream));
+  pl.stopping = v != 0;
+  if (v) pl.stops++;
+  return ODE_OK;
+}
+
+// Launch the pool's serving kernel with `blocks` blocks on its kernel stream,
+// ordered after everything on the copy stream so far (the cleared stop flag,
+// admissions, ring entries).
+int launch_instance(ode_server* s, Pool& pl, int blocks) {
+  if (pl.inst.live || blocks < 1) return ODE_OK;
+  cudaEvent_t ready = nullptr;
+  SCK(s, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ready, s->cstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(pl.kstream, ready, 0);
+  cudaEventDestroy(ready);
+  if (e != cudaSuccess) return scuda(s, e, "instance ordering");
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = pl.cap;
+  a.ld = pl.cap;
+  a.td = pl.td;
+  a.y = pl.y;
+  a.p = pl.p;
+  a.acc = pl.acc;
+  a.status = pl.status;
+  a.ecnt = pl.ecnt;
+  a.nacc = pl.nacc;
+  a.nrej = pl.nrej;
+  a.records = nullptr;
+  a.n_slices = s->slice_periods > 0 ? s->slice_periods : INT_MAX;  // residency quantum
+  a.n_skip = INT_MAX;
+  a.h0 = pl.h0;
+  a.slices_left = pl.left;
+  a.flags = (int*)(pl.ctl + kCtlFlags);
+  a.time_limit_ns = (long long)(pl.time_limit_s * 1e9);
+  a.pr = pl.pr;
+  ServeArgs sv;
+  memset(&sv, 0, sizeof(sv));
+  sv.ring = pl.ring;
+  sv.ring_cap = pl.ring_cap;
+  sv.ctl = pl.ctl;
+  sv.yl = pl.yl;
+  sv.yl_cap = pl.yl_cap;
+  sv.done_cnt = pl.done;
+  sv.done_cap = kMaxReq;
+  sv.owner = pl.owner;
+  sv.idle_ns = kIdleNs;
+  void* args[] = {&a, &sv};
+  SCK(s, cudaLaunchKernel(pl.fn, dim3((unsigned)blocks), dim3(kThreads), args, 0, pl.kstream));
+  SCK(s, cudaEventRecord(pl.inst.ev, pl.kstream));
+  pl.inst.live = true;
+  pl.inst.blocks = blocks;
+  pl.launches++;
+  return ODE_OK;
+}
+
+// Split the GPU between the models that have work, max-min fair: a model's
+// demand is the share of the SMs its unfinished systems fill (one thread per
+// system), and demands are met smallest first, each model getting at most an
+// equal part of what is left.  A model below 0.8 x its share gets another
+// instance if the GPU has room; otherwise the models above 1.5 x their share
+// stop at their next slice boundary (their systems come back through the
+// yield list) and are relaunched at their share once all their instances
+// have exited.
+int manage_instances(ode_server* s) {
+  double demand[kNumModels] = {0}, target[kNumModels] = {0};
+  int order[kNumModels], with_work = 0;
+  for (int m = 0; m < kNumModels; m++) {
+    Pool& pl = s->pools[m];
+    if (!pl.on) continue;
+    if (pl.inst.live) {
+      cudaError_t q = cudaEventQuery(pl.inst.ev);
+      if (q == cudaSuccess) pl.inst.live = false;
+      else if (q != cudaErrorNotReady) return scuda(s, q, "serving kernel");
+    }
+    if (pl.unfinished > 0) {
+      const double blocks = ceil((double)pl.unfinished / kThreads);
+      demand[m] = std::min(1.0, blocks / ((double)pl.bps * s->sms));
+      order[with_work++] = m;
+    }
+  }
+  std::sort(order, order + with_work, [&](int a, int b) { return demand[a] < demand[b]; });
+  double left = 1.0;
+  for (int i = 0; i < with_work; i++) {
+    const int m = order[i];
+    target[m] = std::min(demand[m], left / (with_work - i));
+    left -= target[m];
+  }
+  double used = 0.0;
+  for (Pool& pl : s->pools)
+    if (pl.on) used += share_of(pl, live_blocks(pl), s->sms);
+  for (int m = 0; m < kNumModels; m++) {
+    Pool& pl = s->pools[m];
+    if (!pl.on) continue;
+    const int lb = live_blocks(pl);
+    if (pl.stopping) {
+      if (lb > 0) continue;
+      if (int rc = set_stop(s, pl, 0)) return rc;
+    }
+    if (pl.unfinished <= 0) continue;
+    const double have = share_of(pl, lb, s->sms);
+    if (have >= 0.8 * target[m]) continue;
+    const double want = target[m] - have;
+    if (pl.inst.live) {
+      // one instance per model: a running one below its share is stopped and
+      // relaunched at the share once it has exited (it is not stopped for
+      // less than a quarter of the GPU)
+      if (want >= 0.25 && used + want <= 1.02)
+        if (int rc = set_stop(s, pl, 1)) return rc;
+      continue;
+    }
+    if (used + want <= 1.02) {
+      const int blocks = std::max(1, (int)ceil(target[m] * pl.bps * s->sms));
+      if (int rc = launch_instance(s, pl, blocks)) return rc;
+      used += share_of(pl, blocks, s->sms);
+    } else {
+      for (int o = 0; o < kNumModels; o++) {
+        Pool& po = s->pools[o];
+        if (!po.on || o == m || po.stopping) continue;
+        if (share_of(po, live_blocks(po), s->sms) > 1.5 * target[o] + 1e-9)
+          if (int rc = set_stop(s, po, 1)) return rc;
+      }
+    }
   }
   return ODE_OK;
 }
@@ -345,15 +629,11 @@ int ode_server_create(ode_server** out, int device, long long hbm_budget_bytes, 
   s->device = device;
   s->budget = hbm_budget_bytes;
   s->slice_periods = slice_periods;
-  if (cudaSetDevice(device) != cudaSuccess) {
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess) {
     delete s;
     return ODE_ERR_CUDA;
-  }
-  for (int i = 0; i < kStreams; i++) {
-    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
-      ode_server_destroy(s);
-      return ODE_ERR_CUDA;
-    }
   }
   *out = s;
   return ODE_OK;
@@ -366,7 +646,7 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
   if (!model_dims(cfg->model, &n, &P, &A, &E)) return sfail(s, ODE_ERR_INVALID_ARG, "unknown model");
   Pool& pl = s->pools[cfg->model];
   if (pl.on) return sfail(s, ODE_ERR_INVALID_ARG, "model already added");
-  const void* fn = kernel_of(cfg->model, cfg->scheme, cfg->prec);
+  const void* fn = kernel_for(cfg->model, cfg->scheme, cfg->prec, 3);
   if (!fn) return sfail(s, ODE_ERR_INVALID_ARG, "no kernel for this model / scheme / precision");
   if (capacity < 1) return sfail(s, ODE_ERR_INVALID_ARG, "capacity must be >= 1");
   if (!(h0 > 0.0)) return sfail(s, ODE_ERR_INVALID_ARG, "h0 must be > 0");
@@ -374,7 +654,7 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
       !(cfg->grow_limit <= 1e4) || !(cfg->shrink_limit >= 1e-4) || !(cfg->shrink_limit <= 1.0) ||
       cfg->max_steps_per_slice < 1)
     return sfail(s, ODE_ERR_INVALID_ARG, "invalid step-size settings");
-  const size_t bytes = per_system_bytes(n, P, A, E) * (size_t)capacity + 256;
+  const size_t bytes = per_system_bytes(n, P, A, E) * (size_t)capacity + kCtlWords * 4 + kMaxReq * 4;
   if (s->used + (long long)bytes > s->budget)
     return sfail(s, ODE_ERR_OUT_OF_MEMORY, "pool does not fit in the server's HBM budget");
   if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
@@ -387,6 +667,7 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
   pl.E = E;
   pl.cap = capacity;
   pl.h0 = h0;
+  pl.fn = fn;
   pl.time_limit_s = cfg->time_limit_s;
   Props& pr = pl.pr;
   memset(&pr, 0, sizeof(pr));
@@ -410,21 +691,46 @@ int ode_server_add_model(ode_server* s, const ode_noalloc_settings* cfg, double 
   pr.td_mode = cfg->time_domain_mode;
   pr.max_steps = cfg->max_steps_per_slice;
   for (int i = 0; i < kMaxMC; i++) pr.mc[i] = cfg->model_constants[i];
+  SCK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.bps, fn, kThreads, 0));
+  if (pl.bps < 1) return sfail(s, ODE_ERR_UNSUPPORTED, "serving kernel cannot be resident");
   const size_t C = (size_t)capacity;
+  pl.ring_cap = (unsigned int)capacity;
+  pl.yl_cap = (unsigned int)capacity;
   struct {
     void** p;
     size_t b;
-  } al[] = {{(void**)&pl.td, 2 * C * sizeof(double)},     {(void**)&pl.y, n * C * sizeof(double)},
-            {(void**)&pl.p, P * C * sizeof(double)},      {(void**)&pl.acc, A * C * sizeof(double)},
-            {(void**)&pl.status, C * sizeof(int)},         {(void**)&pl.ecnt, E * C * sizeof(int)},
-            {(void**)&pl.left, C * sizeof(int)},           {(void**)&pl.nacc, C * sizeof(long long)},
-            {(void**)&pl.nrej, C * sizeof(long long)},     {(void**)&pl.head, 256}};
+  } al[] = {{(void**)&pl.td, 2 * C * sizeof(double)},   {(void**)&pl.y, n * C * sizeof(double)},
+            {(void**)&pl.p, P * C * sizeof(double)},    {(void**)&pl.acc, A * C * sizeof(double)},
+            {(void**)&pl.status, C * sizeof(int)},       {(void**)&pl.ecnt, E * C * sizeof(int)},
+            {(void**)&pl.left, C * sizeof(int)},         {(void**)&pl.owner, C * sizeof(int)},
+            {(void**)&pl.nacc, C * sizeof(long long)},   {(void**)&pl.nrej, C * sizeof(long long)},
+            {(void**)&pl.ring, C * sizeof(unsigned int)},
+            {(void**)&pl.yl, C * sizeof(unsigned long long)},
+            {(void**)&pl.ctl, kCtlWords * sizeof(unsigned int)},
+            {(void**)&pl.done, kMaxReq * sizeof(unsigned int)}};
   for (auto& x : al) {
     SCK(s, cudaMalloc(x.p, x.b));
     SCK(s, cudaMemset(*x.p, 0, x.b));
   }
+  SCK(s, cudaMallocHost(&pl.h_ring, C * sizeof(unsigned int)));
+  SCK(s, cudaMallocHost(&pl.h_tail, kTailWords * sizeof(unsigned int)));
+  SCK(s, cudaMallocHost(&pl.h_ctl, kCtlWords * sizeof(unsigned int)));
+  SCK(s, cudaMallocHost(&pl.h_done, kMaxReq * sizeof(unsigned int)));
+  SCK(s, cudaMallocHost(&pl.h_yl, C * sizeof(unsigned long long)));
+  SCK(s, cudaMallocHost(&pl.h_flag, 2 * sizeof(unsigned int)));
+  memset(pl.h_ctl, 0, kCtlWords * sizeof(unsigned int));
+  pl.h_flag[0] = 0;
+  pl.h_flag[1] = 1;
+  SCK(s, cudaStreamCreateWithFlags(&pl.kstream, cudaStreamNonBlocking));
+  SCK(s, cudaEventCreateWithFlags(&pl.inst.ev, cudaEventDisableTiming));
+  for (int i = 0; i < kTailWords; i++) SCK(s, cudaEventCreateWithFlags(&pl.tail_ev[i], cudaEventDisableTiming));
+  SCK(s, cudaEventCreateWithFlags(&pl.snap_ev, cudaEventDisableTiming));
   pl.free_ranges.clear();
   pl.free_ranges[0] = capacity;
+  pl.free_tix.clear();
+  for (int i = kMaxReq - 1; i >= 0; i--) pl.free_tix.push_back(i);
+  pl.slot_req.assign(C, nullptr);
+  pl.tix_base.assign(kMaxReq, 0u);
   pl.bytes = bytes;
   s->used += (long long)bytes;
   pl.on = true;
@@ -448,22 +754,28 @@ int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, co
   r->n = n_systems;
   r->periods = n_periods;
   const size_t n = (size_t)n_systems;
-  cudaError_t e = cudaMallocHost(&r->h_in, (2 + pl.n + pl.P) * n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&r->h_out, (2 + pl.n + pl.A) * n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&r->h_status, n * sizeof(int));
-  if (e == cudaSuccess) e = cudaMallocHost(&r->h_acc_steps, n * sizeof(long long));
+  r->b_in = (2 + pl.n + pl.P) * n * sizeof(double);
+  r->b_meta = 2 * n * sizeof(int);
+  r->b_zero = 2 * n * sizeof(long long);
+  r->b_out = (2 + pl.n + pl.A) * n * sizeof(double);
+  r->b_status = n * sizeof(int);
+  r->b_steps = n * sizeof(long long);
+  PinnedCache& pc = s->pinned;
+  cudaError_t e = pc.get((void**)&r->h_in, r->b_in);
+  if (e == cudaSuccess) e = pc.get((void**)&r->h_meta, r->b_meta);
+  if (e == cudaSuccess) e = pc.get((void**)&r->h_zero, r->b_zero);
+  if (e == cudaSuccess) e = pc.get((void**)&r->h_out, r->b_out);
+  if (e == cudaSuccess) e = pc.get((void**)&r->h_status, r->b_status);
+  if (e == cudaSuccess) e = pc.get((void**)&r->h_acc_steps, r->b_steps);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
-  // timing events only where the chunk length is tuned
-  const unsigned ev_flags = s->slice_periods == 0 ? cudaEventDefault : cudaEventDisableTiming;
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->chunk_ev, ev_flags);
-  if (e == cudaSuccess && s->slice_periods == 0) e = cudaEventCreateWithFlags(&r->start_ev, ev_flags);
   if (e != cudaSuccess) {
-    free_request(r);
+    free_request(pc, r);
     return scuda(s, e, "request buffers");
   }
   memcpy(r->h_in, td, 2 * n * sizeof(double));
   memcpy(r->h_in + 2 * n, y0, pl.n * n * sizeof(double));
   memcpy(r->h_in + (2 + pl.n) * n, p, pl.P * n * sizeof(double));
+  memset(r->h_zero, 0, 2 * n * sizeof(long long));
   r->ticket = s->next_ticket++;
   r->t_submit = now_s();
   s->reqs[r->ticket] = r;
@@ -475,34 +787,22 @@ int ode_server_submit(ode_server* s, int model, int n_systems, int n_periods, co
 int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
   if (!s) return ODE_ERR_INVALID_ARG;
   if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, ODE_ERR_CUDA, "cudaSetDevice failed");
-  int running = 0, waiting = 0;
   // 0. finished copies out free their slots before anything is admitted
   if (int rc = release_harvested(s)) return rc;
+  int running = 0, waiting = 0;
   for (Pool& pl : s->pools) {
     if (!pl.on) continue;
-    // 1. requests whose chunk finished: next chunk, or copy out when done
-    std::vector<Request*> still;
-    for (Request* r : pl.running) {
-      if (r->chunk_inflight) {
-        cudaError_t q = cudaEventQuery(r->chunk_ev);
-        if (q == cudaErrorNotReady) {
-          still.push_back(r);
-          continue;
-        }
-        if (q != cudaSuccess) return scuda(s, q, "chunk");
-        r->chunk_inflight = false;
-        if (s->slice_periods == 0) retune_chunk(r);
-      }
-      if (r->scheduled >= r->periods) {
-        if (int rc = harvest(s, pl, r)) return rc;
-      } else {
-        if (int rc = launch_chunk(s, pl, r)) return rc;
-        still.push_back(r);
+    // 1. a completed snapshot: yielded systems back, finished requests out
+    if (pl.snap_inflight) {
+      cudaError_t q = cudaEventQuery(pl.snap_ev);
+      if (q == cudaSuccess) {
+        if (int rc = take_snapshot(s, pl)) return rc;
+      } else if (q != cudaErrorNotReady) {
+        return scuda(s, q, "snapshot");
       }
     }
-    pl.running.swap(still);
     // 2. admit waiting requests in arrival order while slots are free
-    while (!pl.waiting.empty()) {
+    while (!pl.waiting.empty() && !pl.free_tix.empty()) {
       Request* r = pl.waiting.front();
       const int off = take_range(pl, r->n);
       if (off < 0) break;
@@ -510,10 +810,19 @@ int ode_server_progress(ode_server* s, int* n_running, int* n_waiting) {
       pl.waiting.pop_front();
       if (int rc = admit(s, pl, r)) return rc;
     }
+    // 3. publish systems to the ring
+    if (int rc = publish(s, pl)) return rc;
+  }
+  // 4. kernel instances: relaunch, grow, or stop to rebalance
+  if (int rc = manage_instances(s)) return rc;
+  for (Pool& pl : s->pools) {
+    if (!pl.on) continue;
+    // 5. the next snapshot
+    if (!pl.snap_inflight && (pl.unfinished > 0 || pl.yl_read != pl.known_yield_tail))
+      if (int rc = start_snapshot(s, pl)) return rc;
     running += (int)pl.running.size();
     waiting += (int)pl.waiting.size();
   }
-  // 3. requests whose results have arrived in this pass
   if (int rc = release_harvested(s)) return rc;
   if (n_running) *n_running = running;
   if (n_waiting) *n_waiting = waiting;
@@ -544,24 +853,51 @@ int ode_server_result(ode_server* s, long long ticket, double* td, double* y, do
   if (accepted) memcpy(accepted, r->h_acc_steps, n * sizeof(long long));
   if (latency_s) *latency_s = r->t_done - r->t_submit;
   s->reqs.erase(it);
-  free_request(r);
+  free_request(s->pinned, r);
   return ODE_OK;
 }
 
 int ode_server_destroy(ode_server* s) {
   if (!s) return ODE_OK;
   cudaSetDevice(s->device);
-  for (int i = 0; i < kStreams; i++)
-    if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);
-  for (auto& kv : s->reqs) free_request(kv.second);
+  // running instances stop at their next slice boundary and exit
+  for (Pool& pl : s->pools)
+    if (pl.on && s->cstream) set_stop(s, pl, 1);
+  if (s->cstream) cudaStreamSynchronize(s->cstream);
+  for (Pool& pl : s->pools)
+    if (pl.kstream) cudaStreamSynchronize(pl.kstream);
+  for (auto& kv : s->reqs) free_request(s->pinned, kv.second);
+  s->pinned.release();
   for (Pool& pl : s->pools) {
-    void* ptrs[] = {pl.td, pl.y, pl.p, pl.acc, pl.status, pl.ecnt, pl.left, pl.nacc, pl.nrej, pl.head};
+    void* ptrs[] = {pl.td, pl.y, pl.p, pl.acc, pl.status, pl.ecnt, pl.left, pl.owner, pl.nacc, pl.nrej,
+                    pl.ring, pl.yl, pl.ctl, pl.done};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    void* hp[] = {pl.h_ring, pl.h_tail, pl.h_ctl, pl.h_done, pl.h_yl, pl.h_flag};
+    for (void* p : hp)
+      if (p) cudaFreeHost(p);
+    if (pl.inst.ev) cudaEventDestroy(pl.inst.ev);
+    if (pl.kstream) cudaStreamDestroy(pl.kstream);
+    for (int i = 0; i < kTailWords; i++)
+      if (pl.tail_ev[i]) cudaEventDestroy(pl.tail_ev[i]);
+    if (pl.snap_ev) cudaEventDestroy(pl.snap_ev);
   }
-  for (int i = 0; i < kStreams; i++)
-    if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
+  if (s->cstream) cudaStreamDestroy(s->cstream);
   delete s;
+  return ODE_OK;
+}
+
+int ode_server_stats(const ode_server* s, int model, long long* out) {
+  if (!s || !out || model < 0 || model >= kNumModels) return ODE_ERR_INVALID_ARG;
+  const Pool& pl = s->pools[model];
+  out[0] = pl.launches;
+  out[1] = pl.stops;
+  out[2] = pl.yielded;
+  out[3] = pl.snapshots;
+  out[4] = pl.published;
+  out[5] = pl.finished;
+  out[6] = (long long)pl.flags;
+  out[7] = pl.unfinished;
   return ODE_OK;
 }
 

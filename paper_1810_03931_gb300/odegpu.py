@@ -35,12 +35,12 @@ MODEL_DIMS = {ODE_DUFFING: (2, 2, 7, 1), ODE_KELLER_MIKSIS: (2, 13, 4, 1), ODE_V
 SYMBOLS = (
     "ode_create", "ode_destroy", "ode_query_dims", "ode_num_systems", "ode_set_tolerances",
     "ode_set_events", "ode_set_model_constants", "ode_set_time_domain_mode", "ode_set_step_budget",
-    "ode_set_time_limit", "ode_set_launch", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
+    "ode_set_time_limit", "ode_set_launch", "ode_set_schedule", "ode_linear_set", "ode_random_set", "ode_linear_get", "ode_random_get",
     "ode_solve", "ode_run_periods", "ode_autotune", "ode_synchronize", "ode_get_status", "ode_reset_counters",
     "ode_last_error", "ode_km_coefficients", "ode_cluster_order", "ode_kernel_info", "ode_probe_fma_peak",
     "ode_probe_call_cost", "ode_run_periods_noalloc",
     "ode_server_create", "ode_server_add_model", "ode_server_submit", "ode_server_progress",
-    "ode_server_poll", "ode_server_result", "ode_server_destroy", "ode_server_last_error",
+    "ode_server_poll", "ode_server_result", "ode_server_stats", "ode_server_destroy", "ode_server_last_error",
 )
 
 
@@ -105,7 +105,8 @@ def load(build_if_missing: bool = True):
         "ode_random_get": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
         "ode_solve": [_vp, d, _vp],
         "ode_run_periods": [_vp, d, i, i, _vp, i, _vp],
-        "ode_autotune": [_vp, d, i, _vp, _ip, _ip, _dp],
+        "ode_autotune": [_vp, d, i, _vp, _ip, _ip, _ip, _ip, _dp],
+        "ode_set_schedule": [_vp, i, i],
         "ode_synchronize": [_vp],
         "ode_get_status": [_vp, _vp, _vp, _vp, _vp, i, _vp],
         "ode_reset_counters": [_vp, _vp],
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True):
         "ode_server_progress": [_vp, _ip, _ip],
         "ode_server_poll": [_vp, ll, _ip],
         "ode_server_result": [_vp, ll, _dp, _dp, _dp, _ip, _lp, _dp],
+        "ode_server_stats": [_vp, i, _lp],
         "ode_server_destroy": [_vp],
         "ode_server_last_error": [_vp],
     })
@@ -291,13 +293,21 @@ def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
                                          ODE_PTR_HOST if kind is None else kind, _stream(stream)), s)
 
 
-def ode_autotune(s, h0, n_slices, stream=None):
-    """Returns (block_size, persistent, trial_ms[3][6])."""
-    b, p = ctypes.c_int(), ctypes.c_int()
-    t = np.zeros(18)
-    _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(p),
-                               t.ctypes.data_as(_dp)), s)
-    return b.value, p.value, t.reshape(3, 6)
+def ode_autotune(s, h0, n_slices, stream=None, full=False):
+    """Returns (block, persistent, trial_ms[4][6]); with full=True a dict that
+    adds systems_per_thread, slices_per_launch and the split trials."""
+    b, pr, spt, spl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(27)
+    _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(pr),
+                               ctypes.byref(spt), ctypes.byref(spl), ms.ctypes.data_as(_dp)), s)
+    if full:
+        return dict(block=b.value, persistent=pr.value, systems_per_thread=spt.value,
+                    slices_per_launch=spl.value, trial_ms=ms[:24].reshape(4, 6), split_ms=ms[24:])
+    return b.value, pr.value, ms[:24].reshape(4, 6)
+
+
+def ode_set_schedule(s, systems_per_thread=1, slices_per_launch=0):
+    return _check(load().ode_set_schedule(s, int(systems_per_thread), int(slices_per_launch)), s)
 
 
 def ode_synchronize(s):
@@ -442,6 +452,13 @@ def ode_server_result(s, ticket, n, n_sys, n_acc):
                                      acc.ctypes.data_as(_dp), status.ctypes.data_as(_ip),
                                      accepted.ctypes.data_as(_lp), ctypes.byref(lat)), s)
     return dict(td=td, y=y, acc=acc, status=status, nacc=accepted, latency=lat.value)
+
+
+def ode_server_stats(s, model):
+    out = np.zeros(8, dtype=np.int64)
+    _scheck(load().ode_server_stats(s, int(model), out.ctypes.data_as(_lp)), s)
+    keys = ("launches", "stops", "yielded", "snapshots", "published", "finished", "flags", "unfinished")
+    return dict(zip(keys, (int(x) for x in out)))
 
 
 def ode_server_destroy(s):

@@ -90,19 +90,5 @@ def run_gpu(w, prec=G.ODE_FP64, persistent=0, block=0, record=True, n_transient=
         G.ode_destroy(s)
 
 
-def oracle_config(w):
-    return O.make_config(w["model"], w["scheme"], w["h0"], rtol=w["rtol"], atol=w["atol"], hmax=w["hmax"],
-                         hmin=w["hmin"], grow=w["grow"], shrink=w["shrink"], events_on=w["events_on"],
-                         evt_dir=w["evt_dir"], evt_tol=w["evt_tol"], evt_stop=w["evt_stop"],
-                         max_eq=w["max_eq"], mc=w["mc"] or None, td_mode=w["td_mode"])
-
-
 def run_oracle(w, nthreads=8, record=True, n_transient=None, n_record=None, **cfg_over):
-    n_tr = w["n_transient"] if n_transient is None else n_transient
-    n_rec = w["n_record"] if n_record is None else n_record
-    ww = dict(w)
-    ww.update(cfg_over)
-    cfg = oracle_config(ww)
-    p = km_params_oracle(w) if w["model"] == 1 else w["p"]
-    return O.run(cfg, w["td"], w["y0"], p, None, n_slices=n_tr + n_rec, n_skip=n_tr, record=record,
-                 nthreads=nthreads)
+    return O.run_workload(w, nthreads, record, n_transient, n_record, **cfg_over)

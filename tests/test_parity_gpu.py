@@ -32,6 +32,16 @@ pytestmark = pytest.mark.gpu
 NTHREADS = max(1, min(16, os.cpu_count() or 1))
 
 
+def _report(line):
+    """Print a parity figure (mask fractions, statistics) and, when
+    ODEGPU_PARITY_REPORT names a file, append it there."""
+    print(line)
+    path = os.environ.get("ODEGPU_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(line + "\n")
+
+
 def _rel_close(a, b, rtol, atol):
     return np.abs(a - b) <= atol + rtol * np.abs(b)
 
@@ -89,6 +99,27 @@ def test_duffing_rk4_full_size_parity():
         assert np.all(same_t | _rel_close(rg[:, vrow], ro[:, vrow], 1e-12, 1e-12))
 
 
+def test_duffing_rk4_mixed_time_domains_parity():
+    """The block-shared forcing table serves the systems whose slice matches
+    the grid it was built for; the others rotate their own forcing anchor.
+    Every fourth system here has another time domain (and so another step
+    size and grid); the block's first system alternates between the two
+    kinds, so both paths run in the same warps.  Both kinds match the oracle
+    at the RK4 acceptance (1e-12 relative)."""
+    w = W.duffing_rk4(N=320, n_transient=3, n_record=2)
+    td = w["td"].copy()
+    td[1, 1::4] = 1.5 * math.pi   # shorter slices, other steps
+    td[0, 64::128] = 0.25         # some blocks' first system off the common grid
+    w = dict(w, td=td)
+    o = run_oracle(w, NTHREADS)
+    for persistent in (0, 1):
+        g = run_gpu(w, persistent=persistent, block=64)
+        np.testing.assert_array_equal(g["nacc"], o["nacc"])
+        assert np.all(_rel_close(g["y"], o["y"], 1e-12, 1e-12))
+        for row in (0, 2, 7, 8):
+            assert np.all(_rel_close(g["records"][:, row], o["records"][:, row], 1e-12, 1e-12)), row
+
+
 @pytest.mark.parametrize("persistent", [0, 1, 2])
 def test_duffing_rk4_launch_forms_identical(persistent):
     w = W.duffing_rk4(N=333, n_transient=2, n_record=2)
@@ -129,11 +160,13 @@ def test_duffing_rkck_full_size_sampled():
     w = W.duffing_rkck()
     g = run_gpu(w, autotune=True)
     assert np.all(np.isin(g["status"], [1]))
-    idx = W.sample_indices(w["N"], 40, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, 511, w["N"] - 512, w["N"] - 1))
     ws = W.subset(w, idx)
     mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
     gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
-    assert mask.sum() >= 10
+    _report("duffing_rkck full size: well-conditioned mask keeps %d of %d sampled systems"
+            % (mask.sum(), len(idx)))
+    assert mask.sum() >= 230
     _compare_records(gs, o, mask, 7, 2, tol=1e-8, exact_rows=(6, 9))
     # every system integrated every period
     assert np.all(g["nacc"] > 1088 * 50)
@@ -189,11 +222,13 @@ def test_duffing_lyapunov_full_size_sampled():
     w = W.duffing_lyapunov()
     g = run_gpu(w, autotune=True)
     assert np.all(g["status"] == 1)
-    idx = W.sample_indices(w["N"], 32, corners=(0, 1, w["N"] - 2, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, 1, w["N"] - 2, w["N"] - 1))
     ws = W.subset(w, idx)
     mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(5, 6), rtol=1e-9, agree=1e-7)
     o2 = run_oracle(ws, NTHREADS, rtol=1e-10, atol=1e-10)
-    assert mask.sum() >= 8
+    _report("duffing_lyapunov full size: well-conditioned mask keeps %d of %d sampled systems"
+            % (mask.sum(), len(idx)))
+    assert mask.sum() >= 192
     rg, ro, ro2 = g["records"][:, :, idx][:, :, mask], o["records"][:, :, mask], o2["records"][:, :, mask]
     for row in (0, 2, 5, 6):  # max, min of y1; y1, y2
         np.testing.assert_array_less(np.abs(rg[:, row] - ro[:, row]), 1e-7 * (1 + np.abs(ro[:, row])))
@@ -259,12 +294,13 @@ def test_keller_miksis_protocols_bench_size_sampled(make):
     w = make()
     g = run_gpu(w, autotune=True)
     assert np.all(g["status"] == G.ODE_ST_EVENT_STOP)
-    idx = W.sample_indices(w["N"], 40, corners=(0, 255, w["N"] - 256, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, 255, w["N"] - 256, w["N"] - 1))
     ws = W.subset(w, idx)
     tol = 100 * w["evt_tol"][0]
     mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 6), rtol=1e-10, agree=tol)
     gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
-    assert mask.sum() >= 10
+    _report("%s: well-conditioned mask keeps %d of %d sampled systems" % (w["name"], mask.sum(), len(idx)))
+    assert mask.sum() >= 192
     _compare_records(gs, o, mask, 4, 2, tol=tol)
 
 
@@ -273,22 +309,73 @@ def test_keller_miksis_protocols_bench_size_sampled(make):
 # (Sec. 7.3), per-sweep and persistent launches.
 # ---------------------------------------------------------------------------
 def _valve_stable(w, o, o2, tol):
-    """Systems whose stop reasons, impact counts and end states agree
-    between the oracle at rtol and at rtol / 10."""
+    """Systems whose stop reasons, impact counts, end states and iteration
+    durations agree between two oracle runs (e.g. at rtol and at rtol / 10)."""
     stable = np.all(o["records"][:, 4] == o2["records"][:, 4], axis=0) & (o["status"] == o2["status"])
     stable &= np.all(_rel_close(o["records"][:, 5:8], o2["records"][:, 5:8], tol, tol), axis=(0, 1))
+    d1, d2 = np.diff(o["records"][:, 8], axis=0), np.diff(o2["records"][:, 8], axis=0)
+    stable &= np.all(_rel_close(d1, d2, tol, tol), axis=0)
     return stable
 
 
-def _valve_compare(g, o, stable, tol):
+def _valve_well_conditioned(w, tol):
+    """Valve systems whose stop reasons, impact counts and end states are
+    insensitive both to the integration tolerance (oracle at rtol and at
+    rtol / 10) and to the event tolerance (oracle at tol_E and tol_E / 100):
+    an event that ends a slice or changes the state is located only to
+    |F| <= tol_E, and near grazing impacts that freedom alone can shift which
+    iteration an impact falls in.  Returns the mask and the oracle run."""
+    o = run_oracle(w, NTHREADS)
+    o2 = run_oracle(w, NTHREADS, rtol=w["rtol"] / 10, atol=w["atol"] / 10)
+    o3 = run_oracle(w, NTHREADS, evt_tol=tuple(x / 100 for x in w["evt_tol"]))
+    return _valve_stable(w, o, o2, tol) & _valve_stable(w, o, o3, tol), o
+
+
+def _valve_records_match(rg, ro, tol):
+    """Records [iteration, row] of one system agree: impact counts exactly;
+    maximum, Poincare point and the duration of each iteration within tol
+    (relative + absolute).  The valve is autonomous, so the position along a
+    periodic orbit is neutrally stable and the absolute time of the n-th
+    maximum drifts with every local error (linearly, never damped); the
+    durations of the iterations are what the dynamics fix."""
+    if not np.array_equal(rg[:, 4], ro[:, 4]):
+        return False
+    rows = [0, 5, 6, 7]
+    if not np.all(np.abs(rg[:, rows] - ro[:, rows]) <= tol * (1 + np.abs(ro[:, rows]))):
+        return False
+    dg, do = np.diff(rg[:, 8]), np.diff(ro[:, 8])
+    return bool(np.all(np.abs(dg - do) <= tol * (1 + np.abs(do))))
+
+
+def _valve_compare(g, o, stable, tol, max_shift=4):
+    """GPU against oracle on well-conditioned valve systems.  A system on a
+    periodic orbit (period p iterations) may leave the 1024-iteration
+    transient in another phase than the oracle does -- which of the p
+    iterations comes first is set by the whole transient, and the oracle's
+    own reruns at rtol / 10 and tol_E / 100 can agree on it by chance.  Such
+    a system is accepted when its records equal the oracle's shifted by
+    s <= max_shift iterations (the same orbit, entered one phase apart);
+    the number of them is reported."""
     np.testing.assert_array_equal(g["status"][stable], o["status"][stable])
-    np.testing.assert_array_equal(g["records"][:, 4, stable], o["records"][:, 4, stable])
-    for row in (0, 5, 6, 7, 8):  # max (Poincare section), end state, end time
-        np.testing.assert_array_less(
-            np.abs(g["records"][:, row, stable] - o["records"][:, row, stable]),
-            tol * (1 + np.abs(o["records"][:, row, stable])), err_msg="row %d" % row)
+    shifted = 0
+    for i in np.where(stable)[0]:
+        rg, ro = g["records"][:, :, i], o["records"][:, :, i]
+        if _valve_records_match(rg, ro, tol):
+            continue
+        ok = any(_valve_records_match(rg[sft:], ro[:-sft], tol) or _valve_records_match(rg[:-sft], ro[sft:], tol)
+                 for sft in range(1, max_shift + 1))
+        if not ok:
+            rows = [0, 5, 6, 7]
+            diff = np.abs(rg[:, rows] - ro[:, rows]) / (1 + np.abs(ro[:, rows]))
+            dd = np.abs(np.diff(rg[:, 8]) - np.diff(ro[:, 8])) / (1 + np.abs(np.diff(ro[:, 8])))
+            raise AssertionError("system %d: records differ from the oracle beyond a phase shift: impacts equal "
+                                 "%s, max rel diff of rows 0,5,6,7 %s, of durations %.3e" % (
+                                     i, np.array_equal(rg[:, 4], ro[:, 4]), diff.max(axis=0), dd.max()))
+        shifted += 1
     dev = np.max(np.abs(g["records"][:, 5:8, stable] - o["records"][:, 5:8, stable]))
-    print("valve: max |end state - oracle| over %d points = %.3e" % (stable.sum(), dev))
+    print("valve: %d points compared, %d on the oracle's periodic orbit one or more iterations out of "
+          "phase; max |end state - oracle| = %.3e" % (stable.sum(), shifted, dev))
+    return shifted
 
 
 @pytest.mark.parametrize("persistent", [0, 1])
@@ -372,15 +459,16 @@ def test_valve_full_size_sampled():
         g = gpu_results(s, w, rec)
     finally:
         G.ode_destroy(s)
-    idx = W.sample_indices(w["N"], 24, corners=(0, w["N"] // 2, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, w["N"] // 2, w["N"] - 1))
     ws = W.subset(w, idx)
-    o = run_oracle(ws, NTHREADS)
-    o2 = run_oracle(ws, NTHREADS, rtol=1e-10, atol=1e-10)
     gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
     tol = 100 * w["evt_tol"][0]
-    stable = _valve_stable(ws, o, o2, tol)
-    assert stable.sum() >= 16
-    _valve_compare(gs, o, stable, tol)
+    stable, o = _valve_well_conditioned(ws, tol)
+    assert stable.sum() >= 160
+    shifted = _valve_compare(gs, o, stable, tol)
+    _report("valve full size: well-conditioned mask keeps %d of %d sampled systems; %d of them on the "
+            "oracle's periodic orbit in another phase" % (stable.sum(), len(idx), shifted))
+    assert shifted <= stable.sum() // 20
     # the high-flow-rate end of the sweep rests at the equilibrium (Sec. 7.3)
     assert np.all(g["status"][w["p"][3] > 9.0] == G.ODE_ST_EQUILIBRIUM)
 
@@ -401,11 +489,13 @@ def test_keller_miksis_bench_size_sampled():
     finally:
         G.ode_destroy(s)
     assert np.all(g["status"] == 1)
-    idx = W.sample_indices(w["N"], 24, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, 511, w["N"] - 512, w["N"] - 1))
     ws = W.subset(w, idx)
     mask, o = _nonchaotic(ws, 16, 16, cont_rows=(4, 5), rtol=1e-10, agree=1e-8)
     gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
-    assert mask.sum() >= 12
+    _report("keller_miksis full size: well-conditioned mask keeps %d of %d sampled systems"
+            % (mask.sum(), len(idx)))
+    assert mask.sum() >= 160
     _compare_records(gs, o, mask, 4, 2, tol=1e-8, exact_rows=(6,))
 
 
@@ -475,15 +565,56 @@ def test_fp32_rhs_full_size_sampled_report():
     w = W.duffing_rkck()
     g = run_gpu(w, prec=G.ODE_FP32_RHS, autotune=True)
     assert np.all(g["status"] == 1)
-    idx = W.sample_indices(w["N"], 32, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    idx = W.sample_indices(w["N"], 256, corners=(0, 511, w["N"] - 512, w["N"] - 1))
     ws = W.subset(w, idx)
     mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
     rg, ro = g["records"][:, :, idx][:, :, mask], o["records"][:, :, mask]
     err = {name: float(np.max(np.abs(rg[:, row] - ro[:, row])))
            for name, row in (("event y1", 4), ("event t", 5), ("end y1", 7), ("end y2", 8))}
-    print("FP32_RHS full size, %d of %d sampled points well-conditioned: %s" % (
+    _report("FP32_RHS duffing full size, %d of %d sampled points well-conditioned: %s" % (
         mask.sum(), len(idx), ", ".join("%s %.2e" % kv for kv in err.items())))
     assert mask.sum() >= 10 and max(err.values()) < 1e-3
+
+
+def test_fp32_rhs_valve_full_size_sampled_report():
+    """The binary32 form of the valve sweep at full size (2^16 systems, 1024 +
+    64 iterations, Sec. 7.3): for 256 sampled systems, on the points where the
+    binary64 oracle is well-conditioned (its rtol and rtol / 10 runs agree),
+    the error against the oracle is reported per quantity -- the Poincare
+    maximum y1 and its time, the state at the maximum, the impact count of
+    each iteration and the stop status.  No tolerance is claimed; loose
+    bounds guard against a broken form."""
+    w = W.valve()
+    s = gpu_solver(w, prec=G.ODE_FP32_RHS)
+    try:
+        gpu_load(s, w)
+        G.ode_autotune(s, w["h0"], 2)
+        rec = np.zeros((w["n_record"], 9, w["N"]))
+        G.ode_run_periods(s, w["h0"], w["n_transient"], w["n_record"], rec)
+        G.ode_synchronize(s)
+        g = gpu_results(s, w, rec)
+    finally:
+        G.ode_destroy(s)
+    idx = W.sample_indices(w["N"], 256, corners=(0, w["N"] // 2, w["N"] - 1))
+    ws = W.subset(w, idx)
+    stable, o = _valve_well_conditioned(ws, 100 * w["evt_tol"][0])
+    rg, ro = g["records"][:, :, idx][:, :, stable], o["records"][:, :, stable]
+    err = {}
+    for name, row in (("Poincare max y1", 5), ("y2 at max", 6), ("y3 at max", 7)):
+        d = np.abs(rg[:, row] - ro[:, row])
+        err[name] = (float(np.median(d)), float(np.max(d)))
+    # durations of the iterations (the absolute time drifts along the orbit)
+    d = np.abs(np.diff(rg[:, 8], axis=0) - np.diff(ro[:, 8], axis=0))
+    err["iteration duration"] = (float(np.median(d)), float(np.max(d)))
+    imp_equal = float(np.mean(rg[:, 4] == ro[:, 4]))
+    st_equal = float(np.mean(g["status"][idx][stable] == o["status"][stable]))
+    _report("FP32_RHS valve full size, %d of %d sampled points well-conditioned: %s; impact counts equal "
+            "in %.4f of iterations; status equal in %.4f of systems; accepted steps vs oracle %.3f" % (
+                stable.sum(), len(idx), ", ".join("%s median %.2e max %.2e" % (k, a, b) for k, (a, b) in err.items()),
+                imp_equal, st_equal, g["nacc"][idx].sum() / o["nacc"].sum()))
+    assert stable.sum() >= 160
+    assert np.all(np.isfinite(rg))
+    assert err["Poincare max y1"][0] < 1e-3 and imp_equal > 0.9
 
 
 # ---------------------------------------------------------------------------
@@ -663,10 +794,13 @@ def test_autotune_restores_state_and_keeps_results():
     s = gpu_solver(w)
     try:
         gpu_load(s, w)
-        bs, pers, trials = G.ode_autotune(s, w["h0"], 2)
-        assert bs in (64, 96, 128, 160, 192, 256) and pers in (0, 1, 2)
-        assert trials.shape == (3, 6)
+        t = G.ode_autotune(s, w["h0"], 2, full=True)
+        assert t["block"] in (64, 96, 128, 160, 192, 256) and t["persistent"] in (0, 1, 2)
+        assert t["systems_per_thread"] in (1, 2) and t["slices_per_launch"] in (0, 1)
+        trials = t["trial_ms"]
+        assert trials.shape == (4, 6)
         assert np.all(trials[trials >= 0] > 0) and trials.max() > 0
+        assert t["split_ms"][0] > 0 and t["split_ms"][2] == trials[trials >= 0].min()
         rec = np.zeros((2, 10, w["N"]))
         G.ode_run_periods(s, w["h0"], 2, 2, rec)
         G.ode_synchronize(s)
@@ -675,6 +809,29 @@ def test_autotune_restores_state_and_keeps_results():
             np.testing.assert_array_equal(r[key], ref[key])
     finally:
         G.ode_destroy(s)
+
+
+@pytest.mark.parametrize("spt,spl", [(2, 0), (3, 1), (1, 2), (5, 3)])
+def test_schedule_leaves_results_unchanged(spt, spl):
+    """Several systems per thread (per-sweep launch) and runs split into
+    launches of a few slices give bitwise the same records, states, counters
+    and statuses as one system per thread in one launch; 333 systems leave a
+    ragged last block."""
+    for w in (W.duffing_rkck(37, 9, 3, 2), W.valve(N=333, n_transient=3, n_record=2)):
+        ref = run_gpu(w)
+        n, P, A, E = DIMS[w["model"]]
+        s = gpu_solver(w, block=64)
+        try:
+            G.ode_set_schedule(s, spt, spl)
+            gpu_load(s, w)
+            rec = np.zeros((w["n_record"], A + n + 1, w["N"]))
+            G.ode_run_periods(s, w["h0"], w["n_transient"], w["n_record"], rec)
+            G.ode_synchronize(s)
+            r = gpu_results(s, w, rec)
+        finally:
+            G.ode_destroy(s)
+        for key in ("records", "y", "acc", "td", "nacc", "nrej", "status", "ecnt"):
+            np.testing.assert_array_equal(r[key], ref[key], err_msg=key)
 
 
 def test_kernels_do_not_spill():
@@ -707,3 +864,137 @@ def test_valve_two_events_in_one_step_parity(case):
     np.testing.assert_array_equal(g["status"], o["status"])
     np.testing.assert_array_equal(g["acc"][4], o["acc"][4])  # impacts
     np.testing.assert_allclose(g["y"], o["y"], rtol=1e-8, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Chaotic parameter points (Sec. 7.1.1): no pointwise agreement is possible
+# beyond a short horizon, so the acceptance is (a) agreement over the first
+# periods from the initial conditions and (b) Poincare-section statistics.
+# ---------------------------------------------------------------------------
+def _gpu_records_sampled(w, idx, n_tr, n_rec, autotune=True):
+    """Run the whole sweep w with device-resident records (the bench's launch
+    form, autotuned) and return the records of systems idx only."""
+    import torch
+    n, P, A, E = DIMS[w["model"]]
+    s = gpu_solver(w)
+    try:
+        gpu_load(s, w)
+        if autotune:
+            G.ode_autotune(s, w["h0"], 4)
+        rec = torch.zeros((n_rec, A + n + 1, w["N"]), dtype=torch.float64, device="cuda")
+        G.ode_run_periods(s, w["h0"], n_tr, n_rec, rec)
+        G.ode_synchronize(s)
+        st = np.zeros(w["N"], dtype=np.int32)
+        G.ode_get_status(s, st)
+        sel = torch.as_tensor(np.asarray(idx), device="cuda")
+        return rec.index_select(2, sel).cpu().numpy(), st
+    finally:
+        G.ode_destroy(s)
+
+
+def _distinct(a, digits=6):
+    return len(np.unique(np.round(a, digits)))
+
+
+def _section_statistics(A, B, cols):
+    """Per-system two-sample KS p-values of Poincare sets A[:, i], B[:, i],
+    the median |difference of means|, the median |log variance ratio| and the
+    KS distance between the pooled sets."""
+    from scipy.stats import ks_2samp
+    p = np.array([ks_2samp(A[:, i], B[:, i]).pvalue for i in cols])
+    dm = np.median([abs(A[:, i].mean() - B[:, i].mean()) for i in cols])
+    lv = np.median([abs(math.log(A[:, i].var() / B[:, i].var())) for i in cols])
+    pooled = ks_2samp(A[:, cols].ravel(), B[:, cols].ravel()).statistic
+    return dict(reject=float((p < 0.01).mean()), dmean=float(dm), dlogvar=float(lv), pooled_ks=float(pooled))
+
+
+def test_duffing_chaotic_points_short_horizon_and_poincare_statistics():
+    """The paper's double-well Duffing (delta = +1, Sec. 7.1.1) on the bench's
+    full grid (512 x 256, k in [0.2, 0.3], B in [0.3, 0.5], 2^17 systems,
+    RKCK45 rtol 1e-10, maxima located to 1e-12) in the bench's launch form.
+    Most of these points are chaotic.  512 sampled systems are replayed by
+    the oracle:
+      (a) from the initial conditions, the first three periods agree within
+          100 x rtol on every sampled point (records: located maximum and its
+          time, Poincare point);
+      (b) after 64 transient periods, the Poincare sets y1(2 pi n) of 256
+          recorded periods on the chaotic points (more than 32 distinct
+          values) are compared GPU against oracle with the two-sample KS test
+          at alpha = 0.01, the means and the variances.  Serial correlation
+          makes the nominal 1 % rejection rate meaningless, so the reference
+          is the oracle against itself with atol perturbed by 1e-3 relative (a
+          perturbation at the scale of rounding): the GPU's rejection rate may
+          exceed it by at most 0.05, its median |mean difference| and
+          |log variance ratio| may be at most twice the oracle's, and so may
+          the KS distance between the pooled sets of all chaotic points
+          (pooled, the sets are too correlated for a nominal KS level)."""
+    w = dict(W.duffing_rkck(), mc=(1.0, 1.0, 1.0), name="duffing_double_well_512x256")
+    idx = W.sample_indices(w["N"], 512, corners=(0, 511, w["N"] - 512, w["N"] - 1))
+    ws = W.subset(w, idx)
+    # (a) short horizon
+    g, st = _gpu_records_sampled(w, idx, 0, 3)
+    assert np.all(st == 1)
+    o = run_oracle(ws, NTHREADS, n_transient=0, n_record=3)["records"]
+    tol = 100 * 1e-10
+    for row in (4, 5, 7, 8):
+        assert np.all(np.abs(g[:, row] - o[:, row]) <= tol * (1 + np.abs(o[:, row]))), row
+    np.testing.assert_array_equal(g[:, 6], o[:, 6])  # maxima per period
+    # (b) Poincare statistics after the transient
+    n_tr, n_rec = 64, 256
+    g, st = _gpu_records_sampled(w, idx, n_tr, n_rec)
+    assert np.all(st == 1)
+    o1 = run_oracle(ws, NTHREADS, n_transient=n_tr, n_record=n_rec)["records"]
+    o2 = run_oracle(ws, NTHREADS, n_transient=n_tr, n_record=n_rec, atol=1.001e-10)["records"]
+    Pg, P1, P2 = g[:, 7], o1[:, 7], o2[:, 7]
+    chaotic = np.array([i for i in range(len(idx)) if _distinct(P1[:, i]) > 32])
+    assert len(chaotic) >= 128
+    gpu = _section_statistics(Pg, P1, chaotic)
+    ref = _section_statistics(P2, P1, chaotic)
+    _report("duffing double well full grid: %d of %d sampled points chaotic; GPU vs oracle %s; "
+            "oracle vs perturbed oracle %s" % (len(chaotic), len(idx), gpu, ref))
+    assert gpu["reject"] <= ref["reject"] + 0.05
+    assert gpu["dmean"] <= 2 * ref["dmean"] and gpu["dlogvar"] <= 2 * ref["dlogvar"]
+    assert gpu["pooled_ks"] <= 2 * ref["pooled_ks"] + 0.01
+    # the attractor's range is the same: every GPU section point lies within
+    # the oracle's envelope over all chaotic points, widened by 1 %
+    lo, hi = P1[:, chaotic].min(), P1[:, chaotic].max()
+    assert Pg[:, chaotic].min() >= lo - 0.01 * (hi - lo) and Pg[:, chaotic].max() <= hi + 0.01 * (hi - lo)
+
+
+def test_duffing_bench_grid_conditioning_census():
+    """Every system of the bench sweep (hardening Duffing, 2^17 systems, 1024 +
+    64 periods) integrated on the GPU at rtol and at rtol / 10: the fraction
+    whose records agree within 10 x rtol (the well-conditioned criterion) is
+    reported.  Up to 64 of the systems that disagree are replayed by the
+    oracle, which must find them ill-conditioned too (its own rtol and
+    rtol / 10 runs disagree as well), or agree with the GPU at 100 x rtol."""
+    import torch
+    w = W.duffing_rkck()
+    recs = []
+    for rt in (1e-10, 1e-11):
+        ww = dict(w, rtol=rt, atol=rt)
+        s = gpu_solver(ww)
+        try:
+            gpu_load(s, ww)
+            rec = torch.zeros((w["n_record"], 10, w["N"]), dtype=torch.float64, device="cuda")
+            G.ode_run_periods(s, w["h0"], w["n_transient"], w["n_record"], rec)
+            G.ode_synchronize(s)
+            recs.append(rec)
+        finally:
+            G.ode_destroy(s)
+    a, b = recs[0][:, [4, 5, 7, 8]], recs[1][:, [4, 5, 7, 8]]
+    ok = ((a - b).abs() <= 1e-9 * (1 + b.abs())).all(dim=1).all(dim=0).cpu().numpy()
+    bad = np.where(~ok)[0]
+    _report("duffing_rkck bench grid: %d of %d systems well-conditioned on the GPU (rtol vs rtol/10)"
+            % (ok.sum(), w["N"]))
+    assert ok.mean() > 0.9
+    if len(bad):
+        pick = bad[np.linspace(0, len(bad) - 1, min(64, len(bad))).astype(int)]
+        ws = W.subset(w, pick)
+        mask, o = _nonchaotic(ws, w["n_transient"], w["n_record"], cont_rows=(4, 5, 7, 8), rtol=1e-10)
+        g = recs[0][:, :, torch.as_tensor(pick, device="cuda")].cpu().numpy()
+        agree = np.all(np.abs(g[:, [4, 5, 7, 8]] - o["records"][:, [4, 5, 7, 8]])
+                       <= 1e-8 * (1 + np.abs(o["records"][:, [4, 5, 7, 8]])), axis=(0, 1))
+        _report("  of %d replayed: %d ill-conditioned for the oracle too, %d agree with it at 100 x rtol"
+                % (len(pick), (~mask).sum(), agree.sum()))
+        assert np.all(~mask | agree)

@@ -167,3 +167,35 @@ def test_reused_slot_range_with_distinct_requests_matches_oracle():
         np.testing.assert_array_equal(got["status"], o["status"])
         # the requests differ, so a late copy of a previous occupant would show
         assert not np.array_equal(got["y"], res[list(reqs)[0]]["y"]) or t == list(reqs)[0]
+
+
+def test_late_small_request_overtakes_a_large_one():
+    """Continuous batching in one launch: a large Duffing request (more
+    systems than the serving kernel has threads) holds the GPU; a small request
+    submitted afterwards gets threads as soon as systems are handed back (a
+    residency quantum of 4 periods) and finishes long before the large one,
+    whose results are unchanged (bitwise equal to a plain integration of a
+    sample of its systems)."""
+    srv = G.ode_server_create(0, 8 << 30, 4)
+    try:
+        G.ode_server_add_model(srv, settings_for(W.duffing_rkck(1, 1, 0, 1)), 1e-2, 1 << 17)
+        wb, pb = request(W.DUFFING, 100000, 24, 101)
+        ws, ps = request(W.DUFFING, 10, 2, 102)
+        tb = G.ode_server_submit(srv, W.DUFFING, 24, wb["td"], wb["y0"], pb)
+        t0 = time.time()
+        while time.time() - t0 < 0.3:  # the large request is running
+            G.ode_server_progress(srv)
+            time.sleep(0.0005)
+        ts = G.ode_server_submit(srv, W.DUFFING, 2, ws["td"], ws["y0"], ps)
+        res = drain(srv, {tb: (W.DUFFING, 100000), ts: (W.DUFFING, 10)}, timeout=300)
+        st = G.ode_server_stats(srv, W.DUFFING)
+    finally:
+        G.ode_server_destroy(srv)
+    assert res[ts]["latency"] < 0.5 * res[tb]["latency"], (res[ts]["latency"], res[tb]["latency"])
+    assert st["yielded"] > 0 and st["flags"] == 0 and st["unfinished"] == 0
+    idx = W.sample_indices(100000, 64)
+    wsub = dict(W.subset(wb, idx), n_transient=23, n_record=1)
+    wsub["p"] = np.ascontiguousarray(pb[:, idx])
+    ref = run_gpu(wsub, persistent=0)
+    for key in ("td", "y", "acc", "status", "nacc"):
+        np.testing.assert_array_equal(res[tb][key][..., idx], ref[key], err_msg=key)
