@@ -286,6 +286,8 @@ def run_gpu(args):
         else:
             keys = w["p"][np.ptp(w["p"], axis=1) > 0]
         w = dict(W.subset(w, G.ode_cluster_order(keys)), name=w["name"] + "_clustered")
+    if args.systems is not None and args.systems < w["N"]:
+        w = dict(W.subset(w, np.arange(args.systems)), name=w["name"] + "_first%d" % args.systems)
     if args.n_transient is not None:
         w["n_transient"] = args.n_transient
     if args.n_record is not None:
@@ -306,7 +308,7 @@ def run_gpu(args):
         G.ode_set_model_constants(s, np.array(w["mc"], dtype=np.float64))
     G.ode_set_time_domain_mode(s, w["td_mode"])
     G.ode_set_launch(s, args.block, args.persistent)
-    G.ode_set_schedule(s, args.systems_per_thread, args.slices_per_launch)
+    G.ode_set_schedule(s, args.systems_per_thread, args.slices_per_launch, args.warp_sync)
 
     params = sweep_params(w)
     # resident inputs (HBM) and the records buffer
@@ -331,13 +333,14 @@ def run_gpu(args):
         trials = t["trial_ms"]
         tune = {"block": t["block"], "persistent": t["persistent"],
                 "systems_per_thread": t["systems_per_thread"], "slices_per_launch": t["slices_per_launch"],
+                "warp_sync": t["warp_sync"],
                 "trial_slices": args.tune_slices,
                 "trial_ms": {"per_sweep": [round(x, 2) for x in trials[0]],
                              "per_sweep_2_systems_per_thread": [round(x, 2) for x in trials[1]],
                              "persistent": [round(x, 2) for x in trials[2]],
                              "persistent_lane_order": [round(x, 2) for x in trials[3]],
                              "blocks": [64, 96, 128, 160, 192, 256],
-                             "slices_per_launch_1_half_all": [round(x, 2) for x in t["split_ms"]]}}
+                             "schedule_spl1_half_all_warpsync": [round(x, 2) for x in t["split_ms"]]}}
         args.persistent = t["persistent"]
         args.block = t["block"]
 
@@ -470,7 +473,8 @@ def run_gpu(args):
             "system_periods_per_s": world * w["N"] * (w["n_transient"] + w["n_record"]) / (max_ms * 1e-3),
             "launch": tune if tune else {"block": args.block, "persistent": args.persistent,
                                          "systems_per_thread": args.systems_per_thread,
-                                         "slices_per_launch": args.slices_per_launch},
+                                         "slices_per_launch": args.slices_per_launch,
+                                         "warp_sync": args.warp_sync},
             "clocks": clk,
         }
         if fp32_split is not None:
@@ -728,6 +732,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--systems-per-thread", type=int, default=1, help="with --no-autotune (per-sweep launch)")
     ap.add_argument("--slices-per-launch", type=int, default=0, help="with --no-autotune (0 = all in one)")
+    ap.add_argument("--warp-sync", type=int, default=0, help="with --no-autotune: warp-synchronous slices")
     ap.add_argument("--tune-slices", type=int, default=4)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch from an ncu capture of the same kernel (null if unknown)")
@@ -738,6 +743,7 @@ def main():
                     help="system order: parameter grid, seeded shuffle, or shuffle then ode_cluster_order")
     ap.add_argument("--n-transient", type=int, default=None, help="override (profiling runs)")
     ap.add_argument("--n-record", type=int, default=None, help="override (profiling runs)")
+    ap.add_argument("--systems", type=int, default=None, help="first N systems of the sweep (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

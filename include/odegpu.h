@@ -190,11 +190,14 @@ int ode_set_launch(ode_solver *s, int block_size, int persistent);
  * every thread one system and runs one Solve per launch, Sec. 6.4):
  * systems_per_thread in [1, 64] for the per-sweep launch (thread g of G takes
  * systems g, g + G, g + 2G, ... one after another; the persistent launches
- * ignore it), and slices_per_launch >= 0 for ode_run_periods (the run is split
+ * ignore it), slices_per_launch >= 0 for ode_run_periods (the run is split
  * into launches of that many slices, each launch storing and reloading the
- * whole state; 0 = all slices in one launch).  Results do not depend on
- * either.  Defaults 1 and 0. */
-int ode_set_schedule(ode_solver *s, int systems_per_thread, int slices_per_launch);
+ * whole state; 0 = all slices in one launch), and warp_sync 0 or 1 (1: a
+ * thread whose slice has ended waits until every thread of its warp has
+ * ended its slice, and they start the next one together, so that the threads
+ * of a warp do not drift apart over many slices).  Results do not depend on
+ * any of them.  Defaults 1, 0, 0. */
+int ode_set_schedule(ode_solver *s, int systems_per_thread, int slices_per_launch, int warp_sync);
 
 /* ---- filling and reading the object (Sec. 6.3, 6.10) --------------------- */
 
@@ -251,17 +254,19 @@ int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, dou
  * 192, 256 for each of four forms: per-sweep with 1 and with 2 systems per
  * thread, persistent with queue order 1 and 2 (shapes the kernel cannot
  * launch are skipped) -- then, for the fastest shape, the same slices split
- * into launches of 1 and of ceil(n_slices / 2) slices; every trial is timed
- * with CUDA events on `stream` and starts from the same saved state, which is
- * restored at the end (state, status and counters).  The fastest shape and
- * split are kept (as ode_set_launch and ode_set_schedule would set them).
- * Outputs (may be NULL): block size, persistent value, systems per thread,
- * slices per launch (0 = all), and trial_ms[27] = milliseconds per trial:
- * [form][block] for the 4 x 6 shapes in the order above, then the splits
- * [1 slice, ceil(n_slices / 2) slices, all] (-1 for skipped trials).
- * Allocates a temporary copy of the state.  Synchronous. */
+ * into launches of 1 and of ceil(n_slices / 2) slices, and in one launch with
+ * warp-synchronous slices; every trial is timed with CUDA events on `stream`
+ * and starts from the same saved state, which is restored at the end (state,
+ * status and counters).  The fastest shape and schedule are kept (as
+ * ode_set_launch and ode_set_schedule would set them).  Outputs (may be
+ * NULL): block size, persistent value, systems per thread, slices per launch
+ * (0 = all), warp_sync, and trial_ms[28] = milliseconds per trial: [form][block]
+ * for the 4 x 6 shapes in the order above, then [1 slice per launch,
+ * ceil(n_slices / 2) per launch, all in one launch, all with warp-synchronous
+ * slices] (-1 for skipped trials).  Allocates a temporary copy of the state.
+ * Synchronous. */
 int ode_autotune(ode_solver *s, double h0, int n_slices, void *stream, int *block_size,
-                 int *persistent, int *systems_per_thread, int *slices_per_launch,
+                 int *persistent, int *systems_per_thread, int *slices_per_launch, int *warp_sync,
                  double *trial_ms);
 
 /* Wait for all work this solver enqueued. */

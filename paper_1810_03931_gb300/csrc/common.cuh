@@ -71,6 +71,7 @@ struct KArgs {
                              // 32 * ((c * queue_stride) mod chunks) + 0..31
   int tab_cap;               // RK4 per-sweep launches: entries of the block-shared
                              // forcing table in dynamic shared memory (0 = none)
+  int warp_sync;             // 1: the lanes of a warp start every slice together
   int spt;                   // per-sweep launches: systems per thread (<= 1: one);
                              // thread g takes systems g, g + G, g + 2G, ... (G threads)
   int* flags;                // flags[0] != 0: the watchdog stopped a system

@@ -1023,19 +1023,38 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) o
   // Watchdog: a thread that has run longer than time_limit_ns stops its
   // system with kStTimeout, raises flags[0] and takes no further work, so no
   // launch can run unbounded (e.g. a system crawling at the minimum step).
+  //
+  // Warp-synchronous slices (a.warp_sync): a lane whose slice has ended waits
+  // until every lane of its warp has ended its slice, and then they all
+  // start the next one together.  Lanes of a warp drift apart by their
+  // different step counts; re-aligning them at every slice keeps their
+  // steps, event locations and slice starts (which evaluate the forcing
+  // anchor) in step with each other, at the price of waiting for the
+  // warp's slowest lane in every slice.  Results do not depend on it.
   const unsigned long long t_start = globaltimer_ns();
   unsigned int wd = 0;
+  bool at_boundary = false;
   settle();
   while (__any_sync(0xffffffffu, active)) {
-    if (active) {
+    if (active && !at_boundary) {
       L.trial(a);
-      if (L.status != kStNone) settle();
+      if (L.status != kStNone) {
+        if (a.warp_sync) at_boundary = true;
+        else settle();
+      }
       if (active && a.time_limit_ns > 0 && ((++wd & 1023u) == 0u) &&
           globaltimer_ns() - t_start > (unsigned long long)a.time_limit_ns) {
         L.status = kStTimeout;
         L.store(a);
         atomicExch(a.flags, 1);
         active = false;
+        at_boundary = false;
+      }
+    }
+    if (a.warp_sync && __all_sync(0xffffffffu, !active || at_boundary)) {
+      if (active) {
+        at_boundary = false;
+        settle();
       }
     }
   }

@@ -64,6 +64,7 @@ struct ode_solver {
   int persistent = 0;
   int spt = 1;                  // per-sweep launches: systems per thread
   int slices_per_launch = 0;    // ode_run_periods: slices per launch (0 = all in one)
+  int warp_sync = 0;            // lanes of a warp start every slice together
   double time_limit_s = 600.0;  // watchdog limit per thread and launch
   std::string err;
 };
@@ -387,6 +388,7 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.queue_mode = s->persistent;
   a.queue_stride = queue_stride_for(s->N);
   a.spt = s->persistent ? 1 : s->spt;
+  a.warp_sync = s->warp_sync;
   a.tab_cap = forcing_table_entries(s);
   const size_t smem = (size_t)a.tab_cap * sizeof(double2);
   a.flags = (int*)((char*)s->d_queue + 64);
@@ -613,13 +615,15 @@ int ode_set_launch(ode_solver* s, int block_size, int persistent) {
   return ODE_OK;
 }
 
-int ode_set_schedule(ode_solver* s, int systems_per_thread, int slices_per_launch) {
+int ode_set_schedule(ode_solver* s, int systems_per_thread, int slices_per_launch, int warp_sync) {
   if (check_solver(s)) return ODE_ERR_INVALID_ARG;
   if (systems_per_thread < 1 || systems_per_thread > 64)
     return fail(s, ODE_ERR_INVALID_ARG, "systems_per_thread must be in [1, 64]");
   if (slices_per_launch < 0) return fail(s, ODE_ERR_INVALID_ARG, "slices_per_launch must be >= 0");
+  if (warp_sync != 0 && warp_sync != 1) return fail(s, ODE_ERR_INVALID_ARG, "warp_sync must be 0 or 1");
   s->spt = systems_per_thread;
   s->slices_per_launch = slices_per_launch;
+  s->warp_sync = warp_sync;
   return ODE_OK;
 }
 
@@ -735,7 +739,8 @@ int ode_reset_counters(ode_solver* s, void* stream) {
 const char* ode_last_error(const ode_solver* s) { return s ? s->err.c_str() : g_err.c_str(); }
 
 int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* block_size,
-                 int* persistent, int* systems_per_thread, int* slices_per_launch, double* trial_ms) {
+                 int* persistent, int* systems_per_thread, int* slices_per_launch, int* warp_sync,
+                 double* trial_ms) {
   if (check_solver(s)) return ODE_ERR_INVALID_ARG;
   if (!(h0 > 0.0) || !isfinite(h0)) return fail(s, ODE_ERR_INVALID_ARG, "h0 must be finite and > 0");
   if (n_slices < 1 || n_slices > 1000000) return fail(s, ODE_ERR_INVALID_ARG, "n_slices out of range");
@@ -769,7 +774,7 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
   };
   cudaError_t e = copy_all(true);
   const int old_block = s->block_size, old_pers = s->persistent, old_spt = s->spt,
-            old_spl = s->slices_per_launch;
+            old_spl = s->slices_per_launch, old_ws = s->warp_sync;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -802,6 +807,7 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
       s->persistent = pers;
       s->spt = spt;
       s->slices_per_launch = 0;
+      s->warp_sync = 0;
       float ms;
       if (!trial(&ms)) break;
       if (trial_ms) trial_ms[f * 6 + k] = ms;
@@ -813,25 +819,29 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
       }
     }
   }
-  // slices per launch for the best shape: one slice per launch, half of the
-  // trial's slices per launch, all in one launch (the time measured above)
+  // the split of the slices for the best shape: one slice per launch, half of
+  // the trial's slices per launch, all in one launch (the time measured
+  // above), and all in one launch with warp-synchronous slices
+  int best_ws = 0;
   if (trial_ms)
-    for (int k = 0; k < 3; k++) trial_ms[24 + k] = -1.0;
+    for (int k = 0; k < 4; k++) trial_ms[24 + k] = -1.0;
   if (e == cudaSuccess && rc == ODE_OK) {
     if (trial_ms) trial_ms[26] = best;
-    const int cand[2] = {1, (n_slices + 1) / 2};
-    for (int k = 0; k < 2 && e == cudaSuccess && rc == ODE_OK; k++) {
-      if (cand[k] >= n_slices || (k == 1 && cand[1] == cand[0])) continue;
+    const int cand_spl[3] = {1, (n_slices + 1) / 2, 0}, cand_ws[3] = {0, 0, 1}, slot[3] = {24, 25, 27};
+    for (int k = 0; k < 3 && e == cudaSuccess && rc == ODE_OK; k++) {
+      if (k < 2 && (cand_spl[k] >= n_slices || (k == 1 && cand_spl[1] == cand_spl[0]))) continue;
       s->block_size = best_b;
       s->persistent = best_p;
       s->spt = best_spt;
-      s->slices_per_launch = cand[k];
+      s->slices_per_launch = cand_spl[k];
+      s->warp_sync = cand_ws[k];
       float ms;
       if (!trial(&ms)) break;
-      if (trial_ms) trial_ms[24 + k] = ms;
+      if (trial_ms) trial_ms[slot[k]] = ms;
       if (ms < best) {
         best = ms;
-        best_spl = cand[k];
+        best_spl = cand_spl[k];
+        best_ws = cand_ws[k];
       }
     }
   }
@@ -845,12 +855,15 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
     s->persistent = old_pers;
     s->spt = old_spt;
     s->slices_per_launch = old_spl;
+    s->warp_sync = old_ws;
     return rc != ODE_OK ? rc : cuda_fail(s, e, "ode_autotune");
   }
   s->block_size = best_b;
   s->persistent = best_p;
   s->spt = best_spt;
   s->slices_per_launch = best_spl;
+  s->warp_sync = best_ws;
+  if (warp_sync) *warp_sync = best_ws;
   if (block_size) *block_size = best_b;
   if (persistent) *persistent = best_p;
   if (systems_per_thread) *systems_per_thread = best_spt;

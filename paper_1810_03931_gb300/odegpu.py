@@ -105,8 +105,8 @@ def load(build_if_missing: bool = True):
         "ode_random_get": [_vp, _vp, _vp, i, i, _vp, _vp, _vp, _vp, i, i, _vp],
         "ode_solve": [_vp, d, _vp],
         "ode_run_periods": [_vp, d, i, i, _vp, i, _vp],
-        "ode_autotune": [_vp, d, i, _vp, _ip, _ip, _ip, _ip, _dp],
-        "ode_set_schedule": [_vp, i, i],
+        "ode_autotune": [_vp, d, i, _vp, _ip, _ip, _ip, _ip, _ip, _dp],
+        "ode_set_schedule": [_vp, i, i, i],
         "ode_synchronize": [_vp],
         "ode_get_status": [_vp, _vp, _vp, _vp, _vp, i, _vp],
         "ode_reset_counters": [_vp, _vp],
@@ -295,19 +295,22 @@ def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
 
 def ode_autotune(s, h0, n_slices, stream=None, full=False):
     """Returns (block, persistent, trial_ms[4][6]); with full=True a dict that
-    adds systems_per_thread, slices_per_launch and the split trials."""
-    b, pr, spt, spl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    ms = np.zeros(27)
+    adds systems_per_thread, slices_per_launch, warp_sync and the schedule
+    trials [1 slice per launch, half, all, all warp-synchronous]."""
+    b, pr, spt, spl, ws = (ctypes.c_int() for _ in range(5))
+    ms = np.zeros(28)
     _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(pr),
-                               ctypes.byref(spt), ctypes.byref(spl), ms.ctypes.data_as(_dp)), s)
+                               ctypes.byref(spt), ctypes.byref(spl), ctypes.byref(ws),
+                               ms.ctypes.data_as(_dp)), s)
     if full:
         return dict(block=b.value, persistent=pr.value, systems_per_thread=spt.value,
-                    slices_per_launch=spl.value, trial_ms=ms[:24].reshape(4, 6), split_ms=ms[24:])
+                    slices_per_launch=spl.value, warp_sync=ws.value, trial_ms=ms[:24].reshape(4, 6),
+                    split_ms=ms[24:])
     return b.value, pr.value, ms[:24].reshape(4, 6)
 
 
-def ode_set_schedule(s, systems_per_thread=1, slices_per_launch=0):
-    return _check(load().ode_set_schedule(s, int(systems_per_thread), int(slices_per_launch)), s)
+def ode_set_schedule(s, systems_per_thread=1, slices_per_launch=0, warp_sync=0):
+    return _check(load().ode_set_schedule(s, int(systems_per_thread), int(slices_per_launch), int(warp_sync)), s)
 
 
 def ode_synchronize(s):

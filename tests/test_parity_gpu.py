@@ -796,7 +796,7 @@ def test_autotune_restores_state_and_keeps_results():
         gpu_load(s, w)
         t = G.ode_autotune(s, w["h0"], 2, full=True)
         assert t["block"] in (64, 96, 128, 160, 192, 256) and t["persistent"] in (0, 1, 2)
-        assert t["systems_per_thread"] in (1, 2) and t["slices_per_launch"] in (0, 1)
+        assert t["systems_per_thread"] in (1, 2) and t["slices_per_launch"] in (0, 1) and t["warp_sync"] in (0, 1)
         trials = t["trial_ms"]
         assert trials.shape == (4, 6)
         assert np.all(trials[trials >= 0] > 0) and trials.max() > 0
@@ -811,18 +811,19 @@ def test_autotune_restores_state_and_keeps_results():
         G.ode_destroy(s)
 
 
-@pytest.mark.parametrize("spt,spl", [(2, 0), (3, 1), (1, 2), (5, 3)])
-def test_schedule_leaves_results_unchanged(spt, spl):
-    """Several systems per thread (per-sweep launch) and runs split into
-    launches of a few slices give bitwise the same records, states, counters
-    and statuses as one system per thread in one launch; 333 systems leave a
-    ragged last block."""
+@pytest.mark.parametrize("spt,spl,ws,pers", [(2, 0, 0, 0), (3, 1, 0, 0), (1, 2, 1, 0), (5, 3, 1, 0),
+                                             (1, 0, 1, 0), (1, 0, 1, 1), (1, 2, 1, 2)])
+def test_schedule_leaves_results_unchanged(spt, spl, ws, pers):
+    """Several systems per thread (per-sweep launch), runs split into launches
+    of a few slices and warp-synchronous slices give bitwise the same
+    records, states, counters and statuses as one system per thread in one
+    launch; 333 systems leave a ragged last block."""
     for w in (W.duffing_rkck(37, 9, 3, 2), W.valve(N=333, n_transient=3, n_record=2)):
         ref = run_gpu(w)
         n, P, A, E = DIMS[w["model"]]
-        s = gpu_solver(w, block=64)
+        s = gpu_solver(w, block=64, persistent=pers)
         try:
-            G.ode_set_schedule(s, spt, spl)
+            G.ode_set_schedule(s, spt, spl, ws)
             gpu_load(s, w)
             rec = np.zeros((w["n_record"], A + n + 1, w["N"]))
             G.ode_run_periods(s, w["h0"], w["n_transient"], w["n_record"], rec)
