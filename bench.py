@@ -733,7 +733,8 @@ def main():
     ap.add_argument("--systems-per-thread", type=int, default=1, help="with --no-autotune (per-sweep launch)")
     ap.add_argument("--slices-per-launch", type=int, default=0, help="with --no-autotune (0 = all in one)")
     ap.add_argument("--warp-sync", type=int, default=0, help="with --no-autotune: warp-synchronous slices")
-    ap.add_argument("--tune-slices", type=int, default=4)
+    ap.add_argument("--tune-slices", type=int, default=None,
+                    help="autotuner trial length in slices (default 16 for Duffing sweeps, 4 otherwise)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch from an ncu capture of the same kernel (null if unknown)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -745,6 +746,10 @@ def main():
     ap.add_argument("--n-record", type=int, default=None, help="override (profiling runs)")
     ap.add_argument("--systems", type=int, default=None, help="first N systems of the sweep (profiling runs)")
     args = ap.parse_args()
+    if args.tune_slices is None:
+        # the schedule choices (split, warp-synchronous slices) show over many
+        # slices; a Duffing slice is short, the other models' are long
+        args.tune_slices = 16 if args.workload in ("duffing_rkck", "duffing_rk4") else 4
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":

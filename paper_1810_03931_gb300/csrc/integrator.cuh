@@ -144,6 +144,20 @@ __device__ __forceinline__ void small_angle_f(float x, float U, float& cd, float
   sd = x * fmaf(fmaf(U, b2, b1), U, b0);
 }
 
+// (sin, cos)(omega t) of the harmonic forcing.  A model whose forcing
+// frequency is one period per unit time (omega = 2 pi: Keller-Miksis in its
+// time tau) takes sincospi(2 t), whose argument reduction is exact, instead
+// of rounding 2 pi t first.
+template <class M>
+__device__ __forceinline__ void forcing_sincos(double w, double t, double& s, double& c) {
+  if constexpr (M::kUnitPeriodForcing) {
+    (void)w;
+    sincospi(2.0 * t, &s, &c);
+  } else {
+    sincos(w * t, &s, &c);
+  }
+}
+
 // ---- one trial step --------------------------------------------------------
 // From (t, y) with step hs and the cached first stage k1 = f(t, y), compute
 // the new state ynew and (RKCK45) the error estimate err = hs * sum e_i k_i.
@@ -181,7 +195,7 @@ struct Stepper {
         st.c = C * cd - S * sd;
         st.s = S * cd + C * sd;
       } else {
-        sincos(w * st.t, &st.s, &st.c);
+        forcing_sincos<M>(w, st.t, st.s, st.c);
       }
     } else {
       (void)mct; (void)U; (void)lo;
@@ -445,7 +459,7 @@ struct Lane {
   }
 
   __device__ __forceinline__ void anchor_forcing() {
-    if constexpr (St::kRotate) sincos(w * t, &fS, &fC);
+    if constexpr (St::kRotate) forcing_sincos<M>(w, t, fS, fC);
   }
 
   // Start a slice: Initialization hook (Sec. 6.8), event state at t0 (a
@@ -584,14 +598,23 @@ struct Lane {
   // at the end needs one right-hand side at (t + hs, ynew).  Called once per
   // located event and kept out of line so that its registers do not raise
   // the step loop's register count.
+  // Arguments are scalars and a pointer: array references would make the
+  // caller keep copies of its state and parameters in local memory for the
+  // call (stores on every step).  The parameters are reloaded through L2
+  // (pg[m * ld], the slot's column) and converted to the stage precision.
   static __device__ __noinline__ double predict_root(int js, double t, double hs, double f_old,
-                                                     double f_new, double rate_old,
-                                                     const double (&ynew)[n], const T (&pt)[P],
-                                                     const T (&mct)[3], double Cn, double Sn,
+                                                     double f_new, double rate_old, double y0,
+                                                     double y1, double y2, double y3,
+                                                     const double* pg, long long ld, double mc0,
+                                                     double mc1, double mc2, double Cn, double Sn,
                                                      double w) {
-    T yb[n], f1[n];
+    const double yn[kMaxN] = {y0, y1, y2, y3};
+    T yb[n], f1[n], pt[P];
+    const T mct[3] = {(T)mc0, (T)mc1, (T)mc2};
 #pragma unroll
-    for (int m = 0; m < n; m++) yb[m] = (T)ynew[m];
+    for (int m = 0; m < n; m++) yb[m] = (T)yn[m];
+#pragma unroll
+    for (int m = 0; m < P; m++) pt[m] = (T)__ldcg(pg + m * ld);
     Stage<T> s1;
     if constexpr (St::kRotate) {
       (void)w;
@@ -822,7 +845,9 @@ struct Lane {
           for (int j = 1; j < E; j++)
             if (j == js) fold = F[j];
           const double theta =
-              predict_root(js, t, hs, fold, fj, M::event_rate(js, k1), ynew, pt, mct, Cn, Sn, w);
+              predict_root(js, t, hs, fold, fj, M::event_rate(js, k1), ynew[0], n > 1 ? ynew[1] : 0.0,
+                           n > 2 ? ynew[2] : 0.0, n > 3 ? ynew[3] : 0.0, a.p + sys, (long long)a.ld,
+                           a.pr.mc[0], a.pr.mc[1], a.pr.mc[2], Cn, Sn, w);
           const double delta = 1e-6 * hs;
           theta_a = theta - delta;
           theta_b = theta + delta;
@@ -852,12 +877,15 @@ static __device__ __noinline__ int next_static_system(int sys, int N, int spt) {
   return (nx < N && nx < g + (long long)spt * G) ? (int)nx : N;
 }
 
-// Launch bounds of the integrator kernels: at most ODEGPU_MAX_THREADS per
-// block and at least M::kMinBlocks resident blocks of that size per SM (which
-// caps the registers per thread; more resident warps keep the FP64 pipe fed).
-// Both can be overridden at build time (ODEGPU_MIN_BLOCKS for all models).
-#ifndef ODEGPU_MAX_THREADS
-#define ODEGPU_MAX_THREADS 256
+// Launch bounds of the integrator kernels: at most M::kMaxThreads per block
+// and at least M::kMinBlocks resident blocks of that size per SM, which caps
+// the registers per thread at 65536 / (kMaxThreads x kMinBlocks) (more
+// resident warps keep the FP64 pipe fed).  Both can be overridden at build
+// time (ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS for all models).
+#ifdef ODEGPU_MAX_THREADS
+#define ODEGPU_MAX_THREADS_OF(M) ODEGPU_MAX_THREADS
+#else
+#define ODEGPU_MAX_THREADS_OF(M) M::kMaxThreads
 #endif
 #ifdef ODEGPU_MIN_BLOCKS
 #define ODEGPU_MIN_BLOCKS_OF(M) ODEGPU_MIN_BLOCKS
@@ -867,7 +895,7 @@ static __device__ __noinline__ int next_static_system(int sys, int N, int spt) {
 
 // ---- the kernel --------------------------------------------------------------
 template <class M, int SCHEME, int PREC, bool PERSIST>
-__global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M)) ode_kernel(const KArgs a) {
+__global__ void __launch_bounds__(ODEGPU_MAX_THREADS_OF(M), ODEGPU_MIN_BLOCKS_OF(M)) ode_kernel(const KArgs a) {
   using L_t = Lane<M, SCHEME, PREC>;
   using T = typename L_t::T;
   L_t L;

@@ -64,12 +64,24 @@ __device__ __forceinline__ double recip_nr(double x) {
 // and arguments outside the binary32 seed's range, take pow().
 __device__ __forceinline__ double polytropic_pow(double x, double rx, double e) {
   // 5 e within rounding of an integer (3 * 1.4 is 4.1999999999999993 in
-  // binary64): the exponent is then taken as that integer over 5
+  // binary64): the exponent is then taken as that integer over 5.  The
+  // nearest integer comes from the 1.5 * 2^52 shifter (its low word holds it)
+  // and the range tests compare bit patterns on the integer pipe, so the
+  // test costs four binary64 operations per call.
+  constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
   const double k5 = 5.0 * e;
-  if (fabs(k5 - rint(k5)) <= 1e-12 * k5 && k5 >= 0.0 && k5 <= 60.0 && x > 1e-30 && x < 1e30) {
-    const int k = (int)rint(k5), q = k / 5, r = k % 5;
-    double v = 1.0;
-    for (int i = 0; i < q; i++) v *= rx;
+  const double ks = k5 + kShift;
+  const int k = __double2loint(ks);
+  const bool near_int = dabs_le(k5 - (ks - kShift), 1e-12 * k5);
+  if (near_int && k >= 0 && k <= 60 && dgt(x, 1e-30) && dlt(x, 1e30)) {
+    const int q = k / 5, r = k % 5;
+    // rx^q by repeated squaring (q <= 12)
+    double v = 1.0, b = rx;
+#pragma unroll
+    for (int bit = 0; bit < 4; bit++) {
+      if (q & (1 << bit)) v *= b;
+      if (bit < 3) b *= b;
+    }
     if (r) {
       const double f = rfifth_root(x);
       double fr = f;
@@ -100,7 +112,9 @@ struct Duffing {
   static constexpr int N = 2, P = 2, A = 7, E = 1;
   static constexpr bool kHasFP32 = true;
   static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
+  static constexpr int kMaxThreads = 256;
   static constexpr int kForcing = kCosForcing;  // cos(omega t), omega = mc[2]
+  static constexpr bool kUnitPeriodForcing = false;
 
   template <class T>
   static __device__ __forceinline__ T omega(const T (&mc)[3]) { return mc[2]; }
@@ -145,7 +159,10 @@ struct KellerMiksis {
   static constexpr int N = 2, P = 13, A = 4, E = 1;
   static constexpr bool kHasFP32 = false;
   static constexpr int kMinBlocks = 1;  // launch bound (registers per thread)
+  // 65536 / 384 = 170 registers: six 64-thread blocks per SM, no spills
+  static constexpr int kMaxThreads = 384;
   static constexpr int kForcing = kSinCosForcing;  // sin, cos of 2 pi tau
+  static constexpr bool kUnitPeriodForcing = true;  // omega = 2 pi
 
   template <class T>
   static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)(2.0 * CUDART_PI); }
@@ -159,7 +176,9 @@ struct KellerMiksis {
     const double rx = den * r;
     const double s1 = st.s, c1 = st.c;  // sin, cos of 2 pi tau
     double s2 = 0.0, c2 = 0.0;
-    if (C[6] != 0.0 || C[8] != 0.0) sincos(2.0 * CUDART_PI * C[11] * st.t + C[12], &s2, &c2);
+    // second drive sin(2 pi C11 tau + theta): sincospi reduces its argument
+    // exactly (theta / pi is rounded once; theta = 0 in the paper's scans)
+    if (C[6] != 0.0 || C[8] != 0.0) sincospi(fma(2.0 * C[11], st.t, C[12] * (1.0 / CUDART_PI)), &s2, &c2);
     const double one_c9y2 = 1.0 + C[9] * y2;
     const double num = (C[0] + C[1] * y2) * polytropic_pow(y1, rx, C[10]) - C[2] * one_c9y2 - C[3] * rx -
                        C[4] * y2 * rx - (1.0 - C[9] * y2 * (1.0 / 3.0)) * 1.5 * y2 * y2 -
@@ -195,7 +214,9 @@ struct Valve {
   static constexpr int N = 3, P = 5, A = 5, E = 2;
   static constexpr bool kHasFP32 = true;
   static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
+  static constexpr int kMaxThreads = 256;
   static constexpr int kForcing = kNoForcing;
+  static constexpr bool kUnitPeriodForcing = false;
 
   template <class T>
   static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)0; }
@@ -241,7 +262,9 @@ struct Bounce {
   static constexpr int N = 2, P = 2, A = 6, E = 1;
   static constexpr bool kHasFP32 = true;
   static constexpr int kMinBlocks = 2;  // launch bound (registers per thread)
+  static constexpr int kMaxThreads = 256;
   static constexpr int kForcing = kNoForcing;
+  static constexpr bool kUnitPeriodForcing = false;
 
   template <class T>
   static __device__ __forceinline__ T omega(const T (&)[3]) { return (T)0; }
@@ -291,7 +314,9 @@ struct DuffingLyapunov {
   static constexpr int N = 4, P = 2, A = 5, E = 1;
   static constexpr bool kHasFP32 = false;
   static constexpr int kMinBlocks = 1;  // launch bound (registers per thread)
+  static constexpr int kMaxThreads = 256;
   static constexpr int kForcing = kCosForcing;  // cos(omega t), omega = mc[2]
+  static constexpr bool kUnitPeriodForcing = false;
 
   template <class T>
   static __device__ __forceinline__ T omega(const T (&mc)[3]) { return mc[2]; }

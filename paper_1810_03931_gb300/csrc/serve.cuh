@@ -35,7 +35,7 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
 }
 
 template <class M, int SCHEME, int PREC>
-__global__ void __launch_bounds__(ODEGPU_MAX_THREADS, ODEGPU_MIN_BLOCKS_OF(M))
+__global__ void __launch_bounds__(ODEGPU_MAX_THREADS_OF(M), ODEGPU_MIN_BLOCKS_OF(M))
     serve_kernel(const KArgs a, const ServeArgs sv) {
   using L_t = Lane<M, SCHEME, PREC>;
   using T = typename L_t::T;
