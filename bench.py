@@ -583,7 +583,7 @@ def run_serving(args):
     B.build()
     G.load(build_if_missing=False)
     torch.cuda.set_device(0)
-    caps = {W.DUFFING: 1 << 17, W.VALVE: 1 << 16, W.KELLER_MIKSIS: 1 << 17}
+    caps = {W.DUFFING: 1 << 18, W.VALVE: 1 << 18, W.KELLER_MIKSIS: 1 << 18}
     base = {W.DUFFING: W.duffing_rkck(1, 1, 0, 1), W.VALVE: W.valve(1, 0, 1),
             W.KELLER_MIKSIS: W.keller_miksis(1, 1, 0, 1)}
 
@@ -637,11 +637,14 @@ def run_serving(args):
         finally:
             G.ode_server_destroy(srv)
 
+    service = []  # per-request service times of the plain sequential launches
+
     def drive_sequential(arrivals):
         """Plain per-sweep FP64 launches, one request at a time in arrival order
         (a queue without batching): its own solver, ode_run_periods, read-back."""
         t0 = time.perf_counter()
         lat, steps = [], 0
+        service.clear()
         for k, r in enumerate(reqs):
             now = time.perf_counter() - t0
             if arrivals[k] > now:
@@ -670,6 +673,7 @@ def run_serving(args):
             finally:
                 G.ode_destroy(s)
             lat.append(time.perf_counter() - t0 - arrivals[k])
+            service.append(time.perf_counter() - t0 - max(arrivals[k], now))
             steps += int(acc_steps.sum())
         return time.perf_counter() - t0, np.array(lat), steps
 
@@ -680,18 +684,31 @@ def run_serving(args):
             d["lambda_req_per_s"] = lam
         return d
 
-    # capacity of the plain sequential launches: the whole mix submitted at once
+    def fifo(arrivals):
+        """The plain sequential queue under an arrival process, from the
+        measured service times (a single server taking requests in arrival
+        order: finish_k = max(arrival_k, finish_k-1) + service_k)."""
+        fin, lat = 0.0, []
+        for k in range(len(reqs)):
+            fin = max(arrivals[k], fin) + svc[k]
+            lat.append(fin - arrivals[k])
+        return fin, np.array(lat), steps_seq
+
+    # both forms on the whole mix submitted at once
     span_seq, lat_seq, steps_seq = drive_sequential([0.0] * len(reqs))
+    svc = list(service)
     span_srv, lat_srv, steps_srv = drive([0.0] * len(reqs))
-    capacity = len(reqs) / span_seq
+    capacity = len(reqs) / (span_srv if args.load_basis == "served" else span_seq)
     out = {"closed_batch": {"plain_sequential": summary(span_seq, lat_seq, steps_seq),
                             "served": summary(span_srv, lat_srv, steps_srv)},
-           "capacity_req_per_s": capacity}
+           "capacity_req_per_s": capacity, "load_basis": args.load_basis,
+           "plain_sequential_under_load": "measured" if args.plain_measured else
+           "FIFO queue of the service times measured in the closed batch"}
     unit_arrivals = np.array([r["arrival"] for r in reqs])  # rate 1 request/s
     for frac in args.load_fracs:
         lam = frac * capacity
         arr = list(unit_arrivals / lam)
-        a = summary(*drive_sequential(arr), lam)
+        a = summary(*(drive_sequential(arr) if args.plain_measured else fifo(arr)), lam)
         b_ = summary(*drive(arr), lam)
         out["load_%.2f" % frac] = {"plain_sequential": a, "served": b_}
     line = {"metric": "serving: accepted system-steps/s and p50/p99 request latency",
@@ -700,8 +717,8 @@ def run_serving(args):
             "config": {"workload": "serving mix: Poisson stream over Duffing / Keller-Miksis / valve sweeps",
                        "requests": len(reqs), "sizes": "floor(2^U(0,%d))" % args.max_log2_size,
                        "horizons": "floor(2^U(4,%d)) periods" % args.max_log2_horizon,
-                       "slice_periods_per_tick": args.slice_periods,
-                       "arrival_rates": "fractions of the plain sequential capacity",
+                       "residency_quantum_periods": args.slice_periods,
+                       "arrival_rates": "fractions of the %s capacity" % args.load_basis,
                        "pool_capacity": {"duffing": caps[W.DUFFING], "valve": caps[W.VALVE],
                                          "keller_miksis": caps[W.KELLER_MIKSIS]}},
             "serving": out,
@@ -725,7 +742,12 @@ def main():
     # hour per pass; the default is a bounded mix that keeps the run to minutes
     ap.add_argument("--max-log2-size", type=int, default=14, help="serving: sizes floor(2^U(0, x))")
     ap.add_argument("--max-log2-horizon", type=int, default=8, help="serving: horizons floor(2^U(4, x))")
-    ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 1.0])
+    ap.add_argument("--load-fracs", type=float, nargs="*", default=[0.5, 0.8, 1.0])
+    ap.add_argument("--load-basis", default="served", choices=["served", "plain"],
+                    help="serving: arrival rates as fractions of the served or the plain sequential capacity")
+    ap.add_argument("--plain-measured", action="store_true",
+                    help="serving: run the plain sequential launches under each load instead of "
+                         "queueing their measured service times")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32rhs"])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
