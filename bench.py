@@ -694,10 +694,16 @@ def run_serving(args):
             lat.append(fin - arrivals[k])
         return fin, np.array(lat), steps_seq
 
+    def progress(tag, d):
+        # partial results on stderr, so that a run cut short still reports
+        print("serving %s: %s" % (tag, json.dumps(d)), file=sys.stderr, flush=True)
+
     # both forms on the whole mix submitted at once
+    span_srv, lat_srv, steps_srv = drive([0.0] * len(reqs))
+    progress("served closed batch", summary(span_srv, lat_srv, steps_srv))
     span_seq, lat_seq, steps_seq = drive_sequential([0.0] * len(reqs))
     svc = list(service)
-    span_srv, lat_srv, steps_srv = drive([0.0] * len(reqs))
+    progress("plain closed batch", dict(summary(span_seq, lat_seq, steps_seq), service_s=[round(x, 3) for x in svc]))
     capacity = len(reqs) / (span_srv if args.load_basis == "served" else span_seq)
     out = {"closed_batch": {"plain_sequential": summary(span_seq, lat_seq, steps_seq),
                             "served": summary(span_srv, lat_srv, steps_srv)},
@@ -711,6 +717,7 @@ def run_serving(args):
         a = summary(*(drive_sequential(arr) if args.plain_measured else fifo(arr)), lam)
         b_ = summary(*drive(arr), lam)
         out["load_%.2f" % frac] = {"plain_sequential": a, "served": b_}
+        progress("load %.2f" % frac, out["load_%.2f" % frac])
     line = {"metric": "serving: accepted system-steps/s and p50/p99 request latency",
             "value": steps_srv / span_srv, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic",

@@ -102,6 +102,9 @@ struct ServeArgs {
   unsigned int done_cap;         // entries of done_cnt
   const int* owner;              // [pool capacity] request-table entry of a slot
   long long idle_ns;             // a warp with no work for this long exits
+  int lanes_per_warp;            // threads of a warp that take systems (1 .. 32): few
+                                 // systems are spread thinly, a warp's FP64 issue
+                                 // costing the same whatever its active threads
 };
 
 // Per-model kernel table entry: the kernel function for a (scheme,

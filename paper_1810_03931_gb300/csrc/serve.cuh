@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS_OF(M), ODEGPU_MIN_BLOCKS_OF
   // Claim the next ring entry: slot index, -1 when the ring is empty, -2
   // when the host asked the kernel to stop.  A failed compare-and-swap means
   // another thread claimed that entry; at most 64 attempts per call.
+  const bool claims = (int)(threadIdx.x & 31) < sv.lanes_per_warp;
   auto claim = [&]() -> int {
     if (ld_volatile_u32(stop) != 0u) return -2;
+    if (!claims) return -1;
     unsigned int h = ld_volatile_u32(head);
     for (int it = 0; it < 64; it++) {
       const unsigned int t = ld_volatile_u32(tail);

@@ -116,6 +116,7 @@ struct Request {
 struct Instance {
   cudaEvent_t ev = nullptr;  // completion
   int blocks = 0;
+  int lanes_per_warp = 32;   // threads per warp that take systems
   bool live = false;
 };
 
@@ -311,7 +312,8 @@ unsigned int ring_outstanding(const Pool& pl) {
 }
 
 long long idle_threads(const Pool& pl) {
-  const long long lanes = pl.inst.live ? (long long)pl.inst.blocks * kThreads : 0;
+  const long long lanes =
+      pl.inst.live ? (long long)pl.inst.blocks * (kThreads / 32) * pl.inst.lanes_per_warp : 0;
   if (!pl.snap_valid) return lanes;
   unsigned int done = 0;
   for (int t = 0; t < kMaxReq; t++) done += pl.h_done[t];
@@ -495,7 +497,7 @@ int set_stop(ode_server* s, Pool& pl, int v) {
 // Launch the pool's serving kernel with `blocks` blocks on its kernel stream,
 // ordered after everything on the copy stream so far (the cleared stop flag,
 // admissions, ring entries).
-int launch_instance(ode_server* s, Pool& pl, int blocks) {
+int launch_instance(ode_server* s, Pool& pl, int blocks, int lanes_per_warp) {
   if (pl.inst.live || blocks < 1) return ODE_OK;
   cudaEvent_t ready = nullptr;
   SCK(s, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
@@ -534,25 +536,29 @@ int launch_instance(ode_server* s, Pool& pl, int blocks) {
   sv.done_cap = kMaxReq;
   sv.owner = pl.owner;
   sv.idle_ns = kIdleNs;
+  sv.lanes_per_warp = lanes_per_warp;
   void* args[] = {&a, &sv};
   SCK(s, cudaLaunchKernel(pl.fn, dim3((unsigned)blocks), dim3(kThreads), args, 0, pl.kstream));
   SCK(s, cudaEventRecord(pl.inst.ev, pl.kstream));
   pl.inst.live = true;
   pl.inst.blocks = blocks;
+  pl.inst.lanes_per_warp = lanes_per_warp;
   pl.launches++;
   return ODE_OK;
 }
 
-// Split the GPU between the models that have work, max-min fair: a model's
-// demand is the share of the SMs its unfinished systems fill (one thread per
-// system), and demands are met smallest first, each model getting at most an
-// equal part of what is left.  A model below 0.8 x its share gets another
-// instance if the GPU has room; otherwise the models above 1.5 x their share
-// stop at their next slice boundary (their systems come back through the
-// yield list) and are relaunched at their share once all their instances
-// have exited.
+// Split the GPU between the models that have work, max-min fair in two
+// passes: first the dense demand (the share of the SMs a model's unfinished
+// systems fill at one thread per system), smallest first, each model getting
+// at most an equal part of what is left; then what is left over goes, the
+// same way, to the spread demand (one system per warp).  An instance takes
+// systems on as many threads per warp as its share needs.  A model below
+// 0.8 x its share is started, or stopped and relaunched larger if the GPU has
+// room; otherwise the models above 1.5 x their share stop at their next
+// slice boundary (their systems come back through the yield list) and are
+// relaunched at their share once their instance has exited.
 int manage_instances(ode_server* s) {
-  double demand[kNumModels] = {0}, target[kNumModels] = {0};
+  double demand[kNumModels] = {0}, spread[kNumModels] = {0}, target[kNumModels] = {0};
   int order[kNumModels], with_work = 0;
   for (int m = 0; m < kNumModels; m++) {
     Pool& pl = s->pools[m];
@@ -565,15 +571,30 @@ int manage_instances(ode_server* s) {
     if (pl.unfinished > 0) {
       const double blocks = ceil((double)pl.unfinished / kThreads);
       demand[m] = std::min(1.0, blocks / ((double)pl.bps * s->sms));
+      // spread demand: one system per warp, so that a few slow systems (the
+      // tail of a long request) get a scheduler each instead of sharing one
+      const double wblocks = ceil((double)pl.unfinished / (kThreads / 32));
+      spread[m] = std::min(1.0, wblocks / ((double)pl.bps * s->sms));
       order[with_work++] = m;
     }
   }
-  std::sort(order, order + with_work, [&](int a, int b) { return demand[a] < demand[b]; });
+  // max-min fair split of the dense demand; what is left over goes to the
+  // spread demand (dense packing while the GPU is busy, spreading when SMs
+  // would otherwise idle)
   double left = 1.0;
-  for (int i = 0; i < with_work; i++) {
-    const int m = order[i];
-    target[m] = std::min(demand[m], left / (with_work - i));
-    left -= target[m];
+  for (int pass = 0; pass < 2; pass++) {
+    double want[kNumModels];
+    for (int i = 0; i < with_work; i++) {
+      const int m = order[i];
+      want[m] = pass == 0 ? demand[m] : std::max(0.0, spread[m] - target[m]);
+    }
+    std::sort(order, order + with_work, [&](int a, int b) { return want[a] < want[b]; });
+    for (int i = 0; i < with_work; i++) {
+      const int m = order[i];
+      const double g = std::min(want[m], left / (with_work - i));
+      target[m] += g;
+      left -= g;
+    }
   }
   double used = 0.0;
   for (Pool& pl : s->pools)
@@ -588,6 +609,13 @@ int manage_instances(ode_server* s) {
     }
     if (pl.unfinished <= 0) continue;
     const double have = share_of(pl, lb, s->sms);
+    // a running instance whose claiming threads are far fewer than the
+    // model's unfinished systems is relaunched (more threads per warp)
+    if (pl.inst.live && pl.inst.lanes_per_warp < 32 &&
+        (double)pl.unfinished > 2.0 * lb * (kThreads / 32) * pl.inst.lanes_per_warp) {
+      if (int rc = set_stop(s, pl, 1)) return rc;
+      continue;
+    }
     if (have >= 0.8 * target[m]) continue;
     const double want = target[m] - have;
     if (pl.inst.live) {
@@ -600,7 +628,9 @@ int manage_instances(ode_server* s) {
     }
     if (used + want <= 1.02) {
       const int blocks = std::max(1, (int)ceil(target[m] * pl.bps * s->sms));
-      if (int rc = launch_instance(s, pl, blocks)) return rc;
+      const long long warps = (long long)blocks * (kThreads / 32);
+      const int lpw = (int)std::min<long long>(32, std::max<long long>(1, (pl.unfinished + warps - 1) / warps));
+      if (int rc = launch_instance(s, pl, blocks, lpw)) return rc;
       used += share_of(pl, blocks, s->sms);
     } else {
       for (int o = 0; o < kNumModels; o++) {
