@@ -340,7 +340,8 @@ def run_gpu(args):
                              "persistent": [round(x, 2) for x in trials[2]],
                              "persistent_lane_order": [round(x, 2) for x in trials[3]],
                              "blocks": [64, 96, 128, 160, 192, 256],
-                             "schedule_spl1_half_all_warpsync": [round(x, 2) for x in t["split_ms"]]}}
+                             "schedule_spl1_half_all_warpsync": [round(x, 2) for x in t["split_ms"]],
+                             "warp_sync_per_form_at_its_best_block": [round(x, 2) for x in t["warp_sync_ms"]]}}
         args.persistent = t["persistent"]
         args.block = t["block"]
 

@@ -253,18 +253,19 @@ int ode_run_periods(ode_solver *s, double h0, int n_transient, int n_record, dou
  * launch shape of a fixed candidate list -- block size 64, 96, 128, 160,
  * 192, 256 for each of four forms: per-sweep with 1 and with 2 systems per
  * thread, persistent with queue order 1 and 2 (shapes the kernel cannot
- * launch are skipped) -- then, for the fastest shape, the same slices split
- * into launches of 1 and of ceil(n_slices / 2) slices, and in one launch with
- * warp-synchronous slices; every trial is timed with CUDA events on `stream`
- * and starts from the same saved state, which is restored at the end (state,
- * status and counters).  The fastest shape and schedule are kept (as
- * ode_set_launch and ode_set_schedule would set them).  Outputs (may be
- * NULL): block size, persistent value, systems per thread, slices per launch
- * (0 = all), warp_sync, and trial_ms[28] = milliseconds per trial: [form][block]
- * for the 4 x 6 shapes in the order above, then [1 slice per launch,
- * ceil(n_slices / 2) per launch, all in one launch, all with warp-synchronous
- * slices] (-1 for skipped trials).  Allocates a temporary copy of the state.
- * Synchronous. */
+ * launch are skipped) -- then every form at its fastest block size with
+ * warp-synchronous slices, and the fastest shape of the first search with
+ * the slices split into launches of 1 and of ceil(n_slices / 2) slices; every
+ * trial is timed with CUDA events on `stream` and starts from the same saved
+ * state, which is restored at the end (state, status and counters).  The
+ * fastest of all trials is kept (as ode_set_launch and ode_set_schedule would
+ * set it).  Outputs (may be NULL): block size, persistent value, systems per
+ * thread, slices per launch (0 = all), warp_sync, and trial_ms[32] =
+ * milliseconds per trial: [form][block] for the 4 x 6 shapes in the order
+ * above; then for the fastest of those: [1 slice per launch, ceil(n_slices /
+ * 2) per launch, all in one launch, all with warp-synchronous slices]; then
+ * [form] with warp-synchronous slices at that form's fastest block (-1 for
+ * skipped trials).  Allocates a temporary copy of the state.  Synchronous. */
 int ode_autotune(ode_solver *s, double h0, int n_slices, void *stream, int *block_size,
                  int *persistent, int *systems_per_thread, int *slices_per_launch, int *warp_sync,
                  double *trial_ms);

@@ -789,8 +789,9 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return false;
     return (e = cudaEventElapsedTime(ms, e0, e1)) == cudaSuccess;
   };
-  double best = 1e300;
-  int best_b = 128, best_p = 1, best_spt = 1, best_spl = 0;
+  // fastest block per form (one launch, no warp-synchronous slices)
+  double form_ms[4] = {1e300, 1e300, 1e300, 1e300};
+  int form_b[4] = {0, 0, 0, 0};
   for (int f = 0; f < 4 && e == cudaSuccess && rc == ODE_OK; f++) {
     const int pers = kForms[f][0], spt = kForms[f][1];
     const void* fn = kernel_for(s->model, s->scheme, s->prec, pers ? 1 : 0);
@@ -811,37 +812,67 @@ int ode_autotune(ode_solver* s, double h0, int n_slices, void* stream, int* bloc
       float ms;
       if (!trial(&ms)) break;
       if (trial_ms) trial_ms[f * 6 + k] = ms;
-      if (ms < best) {
-        best = ms;
-        best_b = kBlocks[k];
-        best_p = pers;
-        best_spt = spt;
+      if (ms < form_ms[f]) {
+        form_ms[f] = ms;
+        form_b[f] = kBlocks[k];
       }
     }
   }
-  // the split of the slices for the best shape: one slice per launch, half of
-  // the trial's slices per launch, all in one launch (the time measured
-  // above), and all in one launch with warp-synchronous slices
-  int best_ws = 0;
+  // the fastest shape so far (f0) and the overall choice
+  int f0 = -1;
+  for (int f = 0; f < 4; f++)
+    if (form_b[f] > 0 && (f0 < 0 || form_ms[f] < form_ms[f0])) f0 = f;
+  double best = f0 >= 0 ? form_ms[f0] : 1e300;
+  int best_b = f0 >= 0 ? form_b[f0] : 128, best_p = f0 >= 0 ? kForms[f0][0] : 1,
+      best_spt = f0 >= 0 ? kForms[f0][1] : 1, best_spl = 0, best_ws = 0;
   if (trial_ms)
-    for (int k = 0; k < 4; k++) trial_ms[24 + k] = -1.0;
-  if (e == cudaSuccess && rc == ODE_OK) {
-    if (trial_ms) trial_ms[26] = best;
-    const int cand_spl[3] = {1, (n_slices + 1) / 2, 0}, cand_ws[3] = {0, 0, 1}, slot[3] = {24, 25, 27};
-    for (int k = 0; k < 3 && e == cudaSuccess && rc == ODE_OK; k++) {
-      if (k < 2 && (cand_spl[k] >= n_slices || (k == 1 && cand_spl[1] == cand_spl[0]))) continue;
-      s->block_size = best_b;
-      s->persistent = best_p;
-      s->spt = best_spt;
+    for (int k = 24; k < 32; k++) trial_ms[k] = -1.0;
+  // warp-synchronous slices for every form at its fastest block: whether they
+  // pay depends on the form (a persistent queue mixes systems inside a warp)
+  for (int f = 0; f < 4 && e == cudaSuccess && rc == ODE_OK; f++) {
+    if (form_b[f] == 0) continue;
+    s->block_size = form_b[f];
+    s->persistent = kForms[f][0];
+    s->spt = kForms[f][1];
+    s->slices_per_launch = 0;
+    s->warp_sync = 1;
+    float ms;
+    if (!trial(&ms)) break;
+    if (trial_ms) trial_ms[28 + f] = ms;
+    if (ms < best) {
+      best = ms;
+      best_b = form_b[f];
+      best_p = kForms[f][0];
+      best_spt = kForms[f][1];
+      best_spl = 0;
+      best_ws = 1;
+    }
+  }
+  // the split of the slices for the fastest shape of the first search: one
+  // slice per launch and half of the trial's slices per launch
+  if (f0 >= 0 && e == cudaSuccess && rc == ODE_OK) {
+    if (trial_ms) {
+      trial_ms[26] = form_ms[f0];
+      trial_ms[27] = trial_ms[28 + f0];
+    }
+    const int cand_spl[2] = {1, (n_slices + 1) / 2};
+    for (int k = 0; k < 2 && e == cudaSuccess && rc == ODE_OK; k++) {
+      if (cand_spl[k] >= n_slices || (k == 1 && cand_spl[1] == cand_spl[0])) continue;
+      s->block_size = form_b[f0];
+      s->persistent = kForms[f0][0];
+      s->spt = kForms[f0][1];
       s->slices_per_launch = cand_spl[k];
-      s->warp_sync = cand_ws[k];
+      s->warp_sync = 0;
       float ms;
       if (!trial(&ms)) break;
-      if (trial_ms) trial_ms[slot[k]] = ms;
+      if (trial_ms) trial_ms[24 + k] = ms;
       if (ms < best) {
         best = ms;
+        best_b = form_b[f0];
+        best_p = kForms[f0][0];
+        best_spt = kForms[f0][1];
         best_spl = cand_spl[k];
-        best_ws = cand_ws[k];
+        best_ws = 0;
       }
     }
   }

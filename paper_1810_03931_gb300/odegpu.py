@@ -295,17 +295,19 @@ def ode_run_periods(s, h0, n_transient, n_record, records=None, stream=None):
 
 def ode_autotune(s, h0, n_slices, stream=None, full=False):
     """Returns (block, persistent, trial_ms[4][6]); with full=True a dict that
-    adds systems_per_thread, slices_per_launch, warp_sync and the schedule
-    trials [1 slice per launch, half, all, all warp-synchronous]."""
+    adds systems_per_thread, slices_per_launch, warp_sync, the schedule
+    trials of the fastest shape [1 slice per launch, half, all, all
+    warp-synchronous] and the warp-synchronous trial of every form at its
+    fastest block (warp_sync_ms[4])."""
     b, pr, spt, spl, ws = (ctypes.c_int() for _ in range(5))
-    ms = np.zeros(28)
+    ms = np.zeros(32)
     _check(load().ode_autotune(s, h0, n_slices, _stream(stream), ctypes.byref(b), ctypes.byref(pr),
                                ctypes.byref(spt), ctypes.byref(spl), ctypes.byref(ws),
                                ms.ctypes.data_as(_dp)), s)
     if full:
         return dict(block=b.value, persistent=pr.value, systems_per_thread=spt.value,
                     slices_per_launch=spl.value, warp_sync=ws.value, trial_ms=ms[:24].reshape(4, 6),
-                    split_ms=ms[24:])
+                    split_ms=ms[24:28], warp_sync_ms=ms[28:32])
     return b.value, pr.value, ms[:24].reshape(4, 6)
 
 
