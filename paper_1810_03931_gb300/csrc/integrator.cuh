@@ -972,20 +972,31 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS_OF(M), ODEGPU_MIN_BLOCKS_OF
     }
   }
 
-  // Persistent form, two queue orders (the autotuner tries both):
-  //  mode 1: the device queue hands out slots in warp-aggregated pops -- the
-  //    lanes that ask together take consecutive slots, and slot 32 c + r
-  //    holds system 32 ((c * queue_stride) mod chunks) + r.  So a warp works
-  //    on neighbouring systems of the parameter grid (similar step counts:
-  //    the "clustering" of Sec. 7.2), while chunks popped one after another
-  //    (e.g. by the warps of one SM at the start) lie far apart in the grid,
-  //    which balances cheap and expensive regions across SMs;
+  // Persistent form.  Thread i of the grid starts with system i, as in the
+  // per-sweep grid: the hardware spreads consecutive blocks over the SMs, so
+  // every SM starts with an even sample of the parameter grid (a queue-first
+  // start hands each SM the systems its warps happen to pop first, a random
+  // sample whose cost can differ by tens of percent between SMs when no
+  // refill follows).  The G = gridDim.x * blockDim.x systems after them are
+  // handed out by the device queue as lanes free up, in one of two orders
+  // (the autotuner tries both):
+  //  mode 1: warp-aggregated pops -- the lanes that ask together take
+  //    consecutive slots, and slot 32 c + r holds system G + 32 ((c *
+  //    queue_stride) mod chunks) + r.  So a warp works on neighbouring
+  //    systems of the parameter grid (similar step counts: the "clustering"
+  //    of Sec. 7.2), while chunks popped one after another lie far apart in
+  //    the grid, which balances cheap and expensive regions across SMs;
   //  mode 2: every lane pops the next system in index order on its own (the
   //    lanes of a warp hold systems in the order they freed up).
-  const unsigned int chunks = (unsigned int)((a.N + 31) / 32);
+  const unsigned int G = gridDim.x * blockDim.x;
+  const unsigned int nq = (unsigned int)a.N > G ? (unsigned int)a.N - G : 0u;
+  const unsigned int chunks = (nq + 31u) / 32u;
   auto pop = [&]() -> int {
     namespace cg = cooperative_groups;
-    if (a.queue_mode == 2) return (int)min(atomicAdd(a.queue_head, 1u), (unsigned int)a.N);
+    if (a.queue_mode == 2) {
+      const unsigned int x = atomicAdd(a.queue_head, 1u);
+      return x < nq ? (int)(G + x) : a.N;
+    }
     for (;;) {
       const cg::coalesced_group g = cg::coalesced_threads();
       unsigned int base = 0;
@@ -995,19 +1006,15 @@ __global__ void __launch_bounds__(ODEGPU_MAX_THREADS_OF(M), ODEGPU_MIN_BLOCKS_OF
       const unsigned int c = q >> 5;
       if (c >= chunks) return a.N;  // queue exhausted
       const unsigned int pc = (unsigned int)(((unsigned long long)c * a.queue_stride) % chunks);
-      const int sys = (int)(pc * 32u + (q & 31u));
-      if (sys < a.N) return sys;  // else: the unused tail of the last chunk
+      const unsigned int sys = G + pc * 32u + (q & 31u);
+      if (sys < (unsigned int)a.N) return (int)sys;  // else: the unused tail of the last chunk
     }
   };
   bool active;
   // per-sweep form with several systems per thread: the k-th system of thread
   // g is g + k G (G threads in the grid), so a warp always holds neighbours;
   // k follows from the system index, so no register carries it
-  if constexpr (PERSIST) {
-    L.sys = pop();
-  } else {
-    L.sys = blockIdx.x * blockDim.x + threadIdx.x;
-  }
+  L.sys = blockIdx.x * blockDim.x + threadIdx.x;
   active = L.sys < a.N;
   bool fresh = active;  // a new system is loaded and its slice must begin
 

@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/odegpu.h"
@@ -177,7 +178,6 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   a.h0 = h0;
   a.queue_head = (unsigned int*)(scratch + lay.head);
   a.queue_mode = 1;
-  a.queue_stride = queue_stride_for(n_systems);
   a.flags = (int*)(scratch + lay.head + 64);
   a.time_limit_ns = (long long)(cfg->time_limit_s * 1e9);
   Props& pr = a.pr;
@@ -212,6 +212,8 @@ int launch(const ode_noalloc_settings* cfg, const void* fn, int n, int E, int n_
   long long grid = (long long)bps * sms;
   const long long need = (n_systems + block - 1) / block;
   if (grid > need) grid = need;
+  // the queue holds the systems after the grid's first wave
+  a.queue_stride = queue_stride_for((int)std::max(0LL, (long long)n_systems - grid * block));
   void* args[] = {&a};
   if ((e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, 0, st)) != cudaSuccess)
     return cuda_bad(e);

@@ -386,7 +386,6 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
   a.slices_left = nullptr;
   a.queue_head = s->d_queue;
   a.queue_mode = s->persistent;
-  a.queue_stride = queue_stride_for(s->N);
   a.spt = s->persistent ? 1 : s->spt;
   a.warp_sync = s->warp_sync;
   a.tab_cap = forcing_table_entries(s);
@@ -408,6 +407,9 @@ int integrate(ode_solver* s, double h0, int n_slices, int n_skip, double* record
     grid = (s->N + per_block - 1) / per_block;
   }
   if (grid < 1) grid = 1;
+  // the queue holds the systems after the grid's first wave (thread i starts
+  // with system i)
+  a.queue_stride = queue_stride_for((int)std::max(0LL, (long long)s->N - grid * block));
   void* args[] = {&a};
   CK_CUDA(s, cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, smem, st));
   return ODE_OK;

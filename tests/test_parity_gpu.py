@@ -801,6 +801,22 @@ def test_autotune_restores_state_and_keeps_results():
         assert trials.shape == (4, 6)
         assert np.all(trials[trials >= 0] > 0) and trials.max() > 0
         assert t["split_ms"][0] > 0 and t["split_ms"][2] == trials[trials >= 0].min()
+        # every form that ran was also tried with warp-synchronous slices, and
+        # the choice is the fastest trial of all
+        ran = (trials >= 0).any(axis=1)
+        assert np.all(t["warp_sync_ms"][ran] > 0) and np.all(t["warp_sync_ms"][~ran] == -1)
+        allms = np.concatenate([trials[trials >= 0], t["split_ms"][t["split_ms"] >= 0],
+                                t["warp_sync_ms"][t["warp_sync_ms"] >= 0]])
+        form = {(0, 1): 0, (0, 2): 1, (1, 1): 2, (2, 1): 3}[(t["persistent"], t["systems_per_thread"])]
+        if t["warp_sync"]:
+            chosen = t["warp_sync_ms"][form]
+        elif t["slices_per_launch"] == 1:
+            chosen = t["split_ms"][0]
+        elif t["slices_per_launch"] > 1:
+            chosen = t["split_ms"][1]
+        else:
+            chosen = trials[form][[64, 96, 128, 160, 192, 256].index(t["block"])]
+        assert chosen == allms.min()
         rec = np.zeros((2, 10, w["N"]))
         G.ode_run_periods(s, w["h0"], 2, 2, rec)
         G.ode_synchronize(s)
@@ -809,6 +825,32 @@ def test_autotune_restores_state_and_keeps_results():
             np.testing.assert_array_equal(r[key], ref[key])
     finally:
         G.ode_destroy(s)
+
+
+def test_persistent_refill_beyond_the_first_wave_is_identical():
+    """More systems than the persistent grid has threads (2^17 Duffing systems,
+    64-thread blocks: one wave of 77 824 threads on 152 SMs), so the device
+    queue hands out the systems after the first wave in both orders, with and
+    without warp-synchronous slices: records, end states, step counts and
+    statuses are bitwise those of the per-sweep launch (every system is run
+    exactly once, whoever runs it)."""
+    w = W.duffing_rkck(n_transient=1, n_record=2)
+    ref = run_gpu(w, block=64)
+    for pers in (1, 2):
+        for ws in (0, 1):
+            s = gpu_solver(w, block=64, persistent=pers)
+            try:
+                assert G.ode_kernel_info(w["model"], w["scheme"], G.ODE_FP64, 1, 64)["blocks_per_sm"] * 152 * 64 < w["N"]
+                G.ode_set_schedule(s, 1, 0, ws)
+                gpu_load(s, w)
+                rec = np.zeros((w["n_record"], 10, w["N"]))
+                G.ode_run_periods(s, w["h0"], w["n_transient"], w["n_record"], rec)
+                G.ode_synchronize(s)
+                r = gpu_results(s, w, rec)
+            finally:
+                G.ode_destroy(s)
+            for key in ("records", "y", "acc", "nacc", "status"):
+                np.testing.assert_array_equal(r[key], ref[key], err_msg="%s pers %d ws %d" % (key, pers, ws))
 
 
 @pytest.mark.parametrize("spt,spl,ws,pers", [(2, 0, 0, 0), (3, 1, 0, 0), (1, 2, 1, 0), (5, 3, 1, 0),
@@ -836,13 +878,18 @@ def test_schedule_leaves_results_unchanged(spt, spl, ws, pers):
 
 
 def test_kernels_do_not_spill():
-    for model in (0, 1, 2, 3):
+    """Every integrator kernel launches (at least one resident block per SM)
+    and keeps its state in registers: its local memory is at most the 40-byte
+    call frame of the out-of-line event-root prediction, with no room for
+    spilled registers beyond it."""
+    for model in (0, 1, 2, 3, 4):
         for scheme in (0, 1):
-            for prec in ((0, 1) if model != 1 else (0,)):
+            for prec in ((0, 1) if model in (0, 2, 3) else (0,)):
                 for pers in (0, 1):
                     info = G.ode_kernel_info(model, scheme, prec, pers)
                     assert info["blocks_per_sm"] >= 1
                     assert info["regs"] <= 255
+                    assert info["local_bytes"] <= 40, (model, scheme, prec, pers, info)
 
 
 @pytest.mark.parametrize("case", ["second_not_crossed_at_located_point", "second_crossed_before_it"])
