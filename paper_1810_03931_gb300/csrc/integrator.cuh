@@ -8,7 +8,7 @@
 //    runs many consecutive slices (the iterated Solve of Sec. 7.1.1) so the
 //    state never round-trips through HBM between slices.
 //  * Every loop iteration is ONE trial Runge-Kutta step per lane.  A lane
-//    that is locating an event (bisection in the step size, re-stepping from
+//    that is locating an event (bracketed root search in the step size, re-stepping from
 //    the last accepted point) takes its trial step through the same stage
 //    code as the lanes that take normal steps, so adaptive divergence, event
 //    location and slice / system changes of single lanes never serialise the
@@ -388,8 +388,9 @@ struct Lane {
   int ecnt[E];
   T k1[n];
   double lo, hi, yhi[n];
-  double theta_a, theta_b;  // narrowed bracket to verify first
-  int loc_phase;            // 0: try theta_a, 1: try theta_b, 2: bisect
+  double theta_a, theta_b;  // narrowed bracket to verify first; in phase 2
+                            // theta_a holds F_jstar at lo (F at hi follows from yhi)
+  int loc_phase;            // 0: try theta_a, 1: try theta_b, 2: refine the bracket
   double fC, fS;    // cos, sin of omega t at the lane's t (binary64 forcing)
   double fCn, fSn;  // the same at t + hs of the last normal trial step
   T gC, gS;         // binary32 form: cos, sin of omega t at the lane's t
@@ -632,7 +633,7 @@ struct Lane {
     return hs * hermite_root(f_old, f_new, hs * rate_old, hs * M::event_rate(js, f1));
   }
 
-  // One trial step (normal or bisection).
+  // One trial step (normal, or a locating step inside the event's bracket).
   __device__ __forceinline__ void trial(const KArgs& a) {
     const Props& pr = a.pr;
     double hs;
@@ -642,9 +643,34 @@ struct Lane {
       if (loc_phase == 0) th = theta_a;
       else if (loc_phase == 1) th = theta_b;
       if (!(th > lo && th < hi)) {
-        // a verification point outside the current bracket: bisect
+        // a verification point outside the current bracket: refine.  Before
+        // the first verification lo is 0, where F is the accepted point's.
+        if (loc_phase == 0) {
+          theta_a = F[0];
+#pragma unroll
+          for (int j = 1; j < E; j++)
+            if (j == jstar) theta_a = F[j];
+        }
         loc_phase = 2;
         th = 0.5 * (lo + hi);
+      }
+      if (loc_phase == 2 && (loc_it & 3) != 3) {
+        // the secant of the bracket's end values (the paper's secant
+        // iteration), when it falls strictly inside; every fourth trial
+        // bisects, so the bracket at least halves every four trials whatever
+        // the secant does
+        double Fh[E];
+        M::events(t + hi, yhi, p, Fh);
+        double fhi = Fh[0];
+#pragma unroll
+        for (int j = 1; j < E; j++)
+          if (j == jstar) fhi = Fh[j];
+        // (F at the two ends has opposite signs, so fhi - flo is finite and
+        // nonzero; a reciprocal refined by Newton steps is exact enough for
+        // a trial point, which only has to lie inside the bracket)
+        const double flo = theta_a;
+        const double ts = lo - flo * (hi - lo) * recip_nr(fhi - flo);
+        if (ts > lo && ts < hi) th = ts;
       }
       if (!(th > lo && th < hi) || loc_it >= 200) {
         finish_location(pr);
@@ -726,6 +752,10 @@ struct Lane {
         return;
       }
       const bool pre = dpos(fj) == dpos(fold);
+      // F at the bracket's lower end, kept in theta_a from here on (theta_a
+      // itself has been tried; lo is still 0 after a first verification
+      // point past the root)
+      theta_a = pre ? fj : (loc_phase == 0 ? fold : theta_a);
       if (pre) {
         lo = hs;
       } else {
@@ -827,12 +857,12 @@ struct Lane {
           if (j == js) { fj = Fn[j]; tolj = pr.evt_tol[j]; }
         if (!dabs_le(fj, tolj)) {
           // configuration a of Sec. 4: the step jumped over the zone --
-          // locate by bisection in the step size from (t, y).  The bracket
-          // [0, hs] is first narrowed to theta* +- 1e-6 hs around the root
-          // of the cubic Hermite interpolant of F (end values and slopes;
-          // one extra right-hand side at the step's end), verified by two
-          // trial steps; bisection then runs inside whatever bracket the
-          // verification leaves.
+          // locate the root in the step size from (t, y), bracketed.  The
+          // bracket [0, hs] is first narrowed to theta* +- 1e-6 hs around the
+          // root of the cubic Hermite interpolant of F (end values and
+          // slopes; one extra right-hand side at the step's end), verified by
+          // two trial steps; secant steps, with a bisection every fourth
+          // trial, then run inside whatever bracket the verification leaves.
           locating = true;
           jstar = js;
           loc_it = 0;
@@ -851,7 +881,8 @@ struct Lane {
           const double delta = 1e-6 * hs;
           theta_a = theta - delta;
           theta_b = theta + delta;
-          loc_phase = (theta == theta) ? 0 : 2;  // NaN: plain bisection
+          loc_phase = (theta == theta) ? 0 : 2;  // NaN: refine the whole step
+          if (loc_phase == 2) theta_a = fold;      // F at lo = 0
           return;
         }
       }
